@@ -1,0 +1,197 @@
+/*
+ * da.h -- C ABI of the GB300 cost-and-gradient library for preconditioned
+ * adjoint data assimilation of 2D incompressible Navier-Stokes turbulence
+ * (vorticity form, periodic box [0, 2pi)^2, FP64 throughout).
+ *
+ * What it computes (Ke, You & Wang, "Preconditioned Adjoint Data
+ * Assimilation for Two-Dimensional Decaying and Forced Turbulence"):
+ *   - forward model: Eq. (1), or Eq. (24) with Kolmogorov forcing, in
+ *     vorticity form, Fourier pseudo-spectral in space (2/3-rule square
+ *     truncation |kx|,|ky| <= floor((n-1)/3)), classical RK4 in time;
+ *   - cost: Eq. (2)-(3), J = 1/2 sum over probes x_i and observation times
+ *     t_j of |u(x_i, t_j) - m_ij|^2, velocity sampled at lattice nodes;
+ *   - gradient: the exact discrete adjoint of that scheme (Eq. 11-12 as
+ *     their discrete counterparts), run backward against the stored forward
+ *     stage fields, with the observation mismatch injected at each
+ *     observation step;
+ *   - preconditioner: the control is s = G^{-1/2} c (Eq. 18-19), c the
+ *     scalar field with c_hat = w_hat/|k| (which carries the norm of the
+ *     initial velocity), so w0_hat = |k| W(k)^{1/2} s_hat and
+ *     grad_s J = IDFT(|k| W^{1/2} DFT(grad_{w0} J)); W = G_hat is the
+ *     Fourier kernel of the G-inner product (Eq. 13, 16; kernel families of
+ *     Sec. III.B).
+ *
+ * Conventions
+ *   Physical fields: double [n][n], row-major [iy][ix], x_j = 2 pi j / n.
+ *   Spectral fields: complex double interleaved (re, im), half spectrum
+ *     [n][n/2+1] indexed [q][p] with kx = p, ky = q (q < n/2) or q - n;
+ *     forward transforms are unnormalised, inverse carry 1/n^2.
+ *   A gradient is the Euclidean gradient over grid values; its spectral form
+ *     is the DFT of that grid field.
+ *   Batches: a context holds `batch` independent members that share the
+ *     grid, physics and probe geometry; each member has its own kernel W,
+ *     observations, control and results.  Member b's arrays follow member
+ *     b-1's contiguously.
+ *   Memory: every array argument is a DEVICE pointer owned by the caller
+ *     unless stated otherwise; the context owns only its internal buffers
+ *     (trajectory of stage fields, work arrays, observations, tables).
+ *   Streams: `stream` is a cudaStream_t passed as void*; all work is
+ *     enqueued on it.  One context must not be used from two streams at once.
+ *   Errors: every call returns a da_status and never aborts; da_last_error
+ *     gives the message of the last failure on that context.
+ */
+#ifndef DA_GB300_H
+#define DA_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct da_ctx da_ctx;
+
+typedef enum {
+  DA_OK = 0,
+  DA_EINVAL = 1,     /* invalid argument or unsupported size */
+  DA_ENOMEM = 2,     /* device allocation failed (trajectory too large, ...) */
+  DA_ECUDA = 3,      /* a CUDA call failed; context state is undefined */
+  DA_ETIMEOUT = 4,   /* a bounded device wait gave up */
+  DA_EDIVERGED = 5,  /* non-finite cost or gradient */
+  DA_ENOTCONV = 6    /* the optimiser stopped on a line-search failure */
+} da_status;
+
+/* Grid and time window.  n: points per side, a power of two in [16, 1024].
+ * L: domain side, must be 2 pi (0 means 2 pi).  dt, nsteps: RK4 step and
+ * count.  ckpt_every: 0 stores every stage field of every step for the
+ * adjoint (the default; 128 n^2 bytes per step per member).  batch: members
+ * per context (>= 1). */
+typedef struct {
+  int n;
+  double L;
+  double dt;
+  int nsteps;
+  int ckpt_every;
+  int batch;
+} da_grid;
+
+typedef enum { DA_FORCE_NONE = 0, DA_FORCE_KOLMOGOROV = 1 } da_force_kind;
+
+/* Body force f = (amp sin(nf y), 0) of Eq. (24); vorticity source
+ * -amp nf cos(nf y).  Requires 1 <= nf <= floor((n-1)/3). */
+typedef struct {
+  da_force_kind kind;
+  double amp;
+  int nf;
+} da_forcing;
+
+/* Pointwise velocity probes of Eq. (3) on a uniform lattice: probe
+ * i = r*px + q sits on node (iy, ix) = (r n/py, q n/px).  px must equal py
+ * and divide n.  Observation times are steps j*every, j = 1..nsteps/every
+ * (every must divide nsteps), plus step 0 if include_t0. */
+typedef struct {
+  int px, py;
+  int every;
+  int include_t0;
+} da_obs_operator;
+
+typedef enum {
+  DA_KERNEL_IDENTITY = 0, /* W = 1: the standard adjoint in the velocity metric */
+  DA_KERNEL_EXP_ABS = 1,  /* W = exp(-param |k|) */
+  DA_KERNEL_FRAC = 2,     /* W = |k|^(-2 param): fractional integral, Sec. III.B G_p */
+  DA_KERNEL_EXP_SQ = 3,   /* W = exp(-nu param k^2): heat kernel, Sec. III.B G_e */
+  DA_KERNEL_TABLE = 4     /* W from `table`: HOST pointer to [n][n/2+1] doubles */
+} da_kernel_kind;
+
+typedef struct {
+  da_kernel_kind kind;
+  double param;
+  const double* table;
+} da_kernel;
+
+/* L-BFGS settings of da_assimilate (the paper names L-BFGS, Sec. II.C,
+ * without settings).  Zero fields take the defaults in brackets. */
+typedef struct {
+  int memory;        /* history pairs [10] */
+  double c1, c2;     /* strong Wolfe constants [1e-4, 0.9] */
+  double gtol_rel;   /* stop when |g| <= gtol_rel |g0| [1e-10] */
+  int max_ls_evals;  /* cost-gradient evaluations per line search [20] */
+} da_lbfgs_opts;
+
+/* Create a context.  `kernels` points to grid->batch descriptors (one per
+ * member).  Allocates every device buffer the window needs, so later calls
+ * allocate nothing.  Returns DA_EINVAL for unsupported sizes (message in
+ * *out's last error if *out was created, else via da_last_error(NULL)),
+ * DA_ENOMEM if the trajectory does not fit. */
+da_status da_create(da_ctx** out, const da_grid* grid, double nu, const da_forcing* forcing,
+                    const da_obs_operator* obs, const da_kernel* kernels);
+
+/* Observations m, DEVICE pointer [batch][nt][px*py][2] with nt the number
+ * of observation times; copied into the context on `stream`. */
+da_status da_set_observations(da_ctx* ctx, const double* m, void* stream);
+
+/* Forward solve from controls s [batch][n][n].  omegaT (nullable) receives
+ * the final vorticity half spectrum [batch][n][n/2+1] complex; obs
+ * (nullable) the model observations [batch][nt][px*py][2]. */
+da_status da_forward(da_ctx* ctx, const double* s, double* omegaT, double* obs, void* stream);
+
+/* Cost and gradient: J [batch] (HOST or DEVICE pointer; a host pointer makes
+ * the call wait for the stream) and grad_s [batch][n][n] (device, may be
+ * NULL).  Uses the observations of da_set_observations. */
+da_status da_cost_grad(da_ctx* ctx, const double* s, double* J, double* grad_s, void* stream);
+
+/* Optional extra outputs of the last da_cost_grad / da_adjoint_terminal on
+ * this context: lam0 [batch][n][n/2+1] complex, the DFT of grad_{w0} J
+ * (the physical adjoint at t = 0, Eq. 12); filtered [batch][n][n] the
+ * gradient in the G-metric, IDFT(|k| W DFT(grad_{w0} J)) (Eq. 17 in the
+ * scalar representation).  Either may be NULL. */
+da_status da_last_adjoint(da_ctx* ctx, double* lam0, double* filtered, void* stream);
+
+/* Adjoint of the window driven by a terminal field only (the adjoint
+ * Green's function runs of Sec. IV): lamT [batch][n][n/2+1] complex is the
+ * DFT of a gradient with respect to the final vorticity; returns grad_s
+ * [batch][n][n] (nullable).  Observations are not used. */
+da_status da_adjoint_terminal(da_ctx* ctx, const double* s, const double* lamT, double* grad_s, void* stream);
+
+/* L-BFGS on s (in/out, [batch][n][n]) for up to max_iter iterations, each
+ * member independently.  J_hist: HOST [batch][max_iter+1], the cost at the
+ * start and after every iteration (entries past a member's last iteration
+ * repeat its final cost); iters_done: HOST [batch].  Returns DA_ENOTCONV if
+ * some member stopped on a line-search failure, DA_EDIVERGED on a
+ * non-finite cost.  opts may be NULL. */
+da_status da_assimilate(da_ctx* ctx, double* s, int max_iter, const da_lbfgs_opts* opts, double* J_hist,
+                        int* iters_done, void* stream);
+
+/* Control maps of member kernels: omega0 half spectrum [batch][n][n/2+1]
+ * complex <-> s [batch][n][n].  da_omega_from_control applies P |k| W^{1/2};
+ * da_control_from_omega its inverse on the retained set. */
+da_status da_omega_from_control(da_ctx* ctx, const double* s, double* omega0, void* stream);
+da_status da_control_from_omega(da_ctx* ctx, const double* omega0, double* s, void* stream);
+
+/* Number of observation times of the context (nt). */
+int da_num_obs_times(const da_ctx* ctx);
+
+/* Device bytes held by the context. */
+unsigned long long da_device_bytes(const da_ctx* ctx);
+
+/* Number of kernel launches the context has issued so far. */
+unsigned long long da_launch_count(const da_ctx* ctx);
+
+/* Event timing of one class of pass kernels, for roofline reports:
+ * kernel_class 0 off, 1 forward row pass, 2 forward column pass, 3 adjoint
+ * row pass, 4 adjoint column pass.  While on, every launch of that class is
+ * bracketed by two CUDA events on the launch stream. */
+da_status da_time_kernels(da_ctx* ctx, int kernel_class);
+
+/* Total device time (ms) and launch count of the timed class since the last
+ * call; waits for the last recorded event. */
+da_status da_kernel_time(da_ctx* ctx, double* total_ms, unsigned long long* launches);
+
+/* Message of the last failure on ctx (NULL: the last failed da_create). */
+const char* da_last_error(const da_ctx* ctx);
+
+/* Free every device buffer of ctx; waits for no stream. */
+void da_destroy(da_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,780 @@
+// da_api.cu -- the C ABI of include/da.h: context, validation, buffers and
+// the launch sequence of the forward solve, the adjoint sweep and the
+// optimiser.  All arithmetic of the path runs in the kernels of
+// kernels.cuh / blas.cuh; this file only orders launches and moves scalars.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/da.h"
+#include "blas.cuh"
+#include "linesearch.h"
+#include "ops.h"
+
+using da::Dev;
+using da::Ops;
+
+struct da_ctx {
+  int device = 0;
+  int n = 0, nsteps = 0, ckpt = 0, B = 1;
+  double dt = 0, nu = 0;
+  da_forcing force{};
+  da_obs_operator obs{};
+  int nt = 0, P = 0;
+  const Ops* ops = nullptr;
+  Dev dev{};
+  std::vector<void*> allocs;
+  unsigned long long bytes = 0;
+  unsigned long long launches = 0;
+  bool have_obs = false;
+  bool have_adj = false;
+  std::string err;
+  // optimiser buffers (allocated on first da_assimilate)
+  double *x = nullptr, *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr, *S = nullptr, *Y = nullptr;
+  double *part = nullptr, *dots = nullptr, *scal = nullptr;
+  void** ptrs = nullptr;
+  int mem = 0;
+  // event timing of one kernel class
+  int timed_class = 0;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+};
+
+static std::string g_create_error;
+
+#define DA_TRY_CUDA(ctx, call)                                                                    \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail((ctx), DA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+static da_status fail(da_ctx* c, da_status s, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_create_error = msg;
+  return s;
+}
+
+static da_status check_launch(da_ctx* c, unsigned long long nlaunch = 1) {
+  c->launches += nlaunch;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, DA_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return DA_OK;
+}
+
+// Brackets one launch of kernel class `cls` with events when that class is timed.
+struct Timed {
+  da_ctx* c;
+  bool on;
+  cudaStream_t st;
+  Timed(da_ctx* c_, int cls, cudaStream_t s) : c(c_), on(c_->timed_class == cls), st(s) {
+    if (!on) return;
+    if (c->ev_used + 2 > c->ev.size()) {
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+          on = false;
+          return;
+        }
+        c->ev.push_back(e);
+      }
+    }
+    cudaEventRecord(c->ev[c->ev_used], st);
+  }
+  ~Timed() {
+    if (!on) return;
+    cudaEventRecord(c->ev[c->ev_used + 1], st);
+    c->ev_used += 2;
+  }
+};
+
+template <typename T>
+static da_status dalloc(da_ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return DA_OK;
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char buf[160];
+    snprintf(buf, sizeof buf, "cudaMalloc of %.3f GB failed: %s", count * sizeof(T) / 1e9, cudaGetErrorString(e));
+    return fail(c, DA_ENOMEM, buf);
+  }
+  c->allocs.push_back(v);
+  c->bytes += count * sizeof(T);
+  *p = static_cast<T*>(v);
+  return DA_OK;
+}
+
+// exp(-2 pi i t / m), t < m, rounded from long double.
+static std::vector<double2> roots_of_unity(int m) {
+  std::vector<double2> w(m);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int t = 0; t < m; ++t) {
+    long double a = -2.0L * pi * (long double)t / (long double)m;
+    w[t] = make_double2((double)cosl(a), (double)sinl(a));
+  }
+  return w;
+}
+
+static int obs_slot_host(const da_ctx* c, int k) {
+  if (k == 0) return c->obs.include_t0 ? 0 : -1;
+  if (k % c->obs.every) return -1;
+  return k / c->obs.every - 1 + (c->obs.include_t0 ? 1 : 0);
+}
+
+extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, const da_forcing* forcing,
+                               const da_obs_operator* obs, const da_kernel* kernels) {
+  if (!out) return fail(nullptr, DA_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!grid || !obs || !kernels) return fail(nullptr, DA_EINVAL, "grid, obs and kernels must not be NULL");
+  const int n = grid->n;
+  const Ops* ops = da::ops_for(n);
+  if (!ops) return fail(nullptr, DA_EINVAL, "n must be a power of two in [16, 1024]");
+  if (grid->L != 0.0 && std::fabs(grid->L - 2.0 * M_PI) > 1e-12) return fail(nullptr, DA_EINVAL, "L must be 2 pi");
+  if (!(grid->dt > 0.0) || !std::isfinite(grid->dt)) return fail(nullptr, DA_EINVAL, "dt must be positive");
+  if (grid->nsteps < 1) return fail(nullptr, DA_EINVAL, "nsteps must be >= 1");
+  if (grid->batch < 1) return fail(nullptr, DA_EINVAL, "batch must be >= 1");
+  if (grid->ckpt_every > 0) return fail(nullptr, DA_EINVAL, "checkpointing (ckpt_every > 0) is not available; use 0 (store all) or -1 (forward only)");
+  if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(nullptr, DA_EINVAL, "nu must be >= 0");
+  da_forcing f{DA_FORCE_NONE, 0.0, 0};
+  if (forcing) f = *forcing;
+  if (f.kind != DA_FORCE_NONE && f.kind != DA_FORCE_KOLMOGOROV) return fail(nullptr, DA_EINVAL, "unknown forcing kind");
+  if (f.kind == DA_FORCE_KOLMOGOROV && (f.nf < 1 || f.nf > ops->K))
+    return fail(nullptr, DA_EINVAL, "forcing wavenumber must be in [1, floor((n-1)/3)]");
+  if (obs->px != obs->py) return fail(nullptr, DA_EINVAL, "px must equal py");
+  if (obs->px < 1 || obs->px > da::Geo<16>::PMAX || n % obs->px) return fail(nullptr, DA_EINVAL, "px must divide n and be <= 64");
+  if (obs->every < 1 || grid->nsteps % obs->every) return fail(nullptr, DA_EINVAL, "obs.every must divide nsteps");
+  for (int b = 0; b < grid->batch; ++b) {
+    const da_kernel& k = kernels[b];
+    if (k.kind < DA_KERNEL_IDENTITY || k.kind > DA_KERNEL_TABLE) return fail(nullptr, DA_EINVAL, "unknown kernel kind");
+    if (k.kind == DA_KERNEL_TABLE && !k.table) return fail(nullptr, DA_EINVAL, "table kernel needs a table");
+    if (!std::isfinite(k.param)) return fail(nullptr, DA_EINVAL, "kernel parameter must be finite");
+  }
+
+  da_ctx* c = new da_ctx();
+  cudaGetDevice(&c->device);
+  c->n = n;
+  c->nsteps = grid->nsteps;
+  c->ckpt = grid->ckpt_every;
+  c->B = grid->batch;
+  c->dt = grid->dt;
+  c->nu = nu;
+  c->force = f;
+  c->obs = *obs;
+  c->P = obs->px;
+  c->nt = grid->nsteps / obs->every + (obs->include_t0 ? 1 : 0);
+  c->ops = ops;
+
+  Dev& d = c->dev;
+  d.B = c->B;
+  d.nsteps = c->nsteps;
+  d.every = obs->every;
+  d.include_t0 = obs->include_t0 ? 1 : 0;
+  d.px = c->P;
+  d.nt = c->nt;
+  d.dt = c->dt;
+  d.nu = nu;
+  d.force = f.kind == DA_FORCE_KOLMOGOROV;
+  d.amp = f.amp;
+  d.nf = f.nf;
+
+  const size_t B = c->B, N = n, comp = B * ops->Kr * ops->Kc, P2 = (size_t)c->P * c->P;
+  da_status s = DA_OK;
+  auto A = [&](da_status st) {
+    if (s == DA_OK) s = st;
+  };
+  A(dalloc(c, &d.W, comp));
+  A(dalloc(c, &d.Acc, comp));
+  A(dalloc(c, &d.Y, comp));
+  A(dalloc(c, &d.KB, comp));
+  A(dalloc(c, &d.LamBar, comp));
+  A(dalloc(c, &d.Sum, comp));
+  A(dalloc(c, &d.Mx, B * 4 * N * ops->Kc));
+  A(dalloc(c, &d.Mn, B * N * ops->Kc));
+  A(dalloc(c, &d.obs, B * c->nt * P2 * 2));
+  A(dalloc(c, (double**)&d.mobs, B * c->nt * P2 * 2));
+  A(dalloc(c, &d.res, B * c->nt * P2 * 2));
+  A(dalloc(c, &d.J, B));
+  A(dalloc(c, (double**)&d.mult, comp));
+  A(dalloc(c, (double2**)&d.tw, N));
+  A(dalloc(c, (double2**)&d.twP, (size_t)c->P));
+  if (c->ckpt == 0) A(dalloc(c, &d.traj, B * (size_t)c->nsteps * 16 * N * N));
+  int* d_kind = nullptr;
+  double *d_param = nullptr, *d_table = nullptr;
+  A(dalloc(c, &d_kind, B));
+  A(dalloc(c, &d_param, B));
+  bool any_table = false;
+  for (int b = 0; b < c->B; ++b) any_table |= kernels[b].kind == DA_KERNEL_TABLE;
+  if (any_table) A(dalloc(c, &d_table, B * N * (N / 2 + 1)));
+  if (s != DA_OK) {
+    g_create_error = c->err;
+    da_destroy(c);
+    return s;
+  }
+  // constant tables: twiddles of the FFT plan and of the probe lattice
+  std::vector<double2> tw = roots_of_unity(n), twP = roots_of_unity(c->P);
+  std::vector<int> kind(B);
+  std::vector<double> param(B);
+  for (size_t b = 0; b < B; ++b) {
+    kind[b] = kernels[b].kind;
+    param[b] = kernels[b].param;
+  }
+  cudaError_t e = cudaMemcpy((void*)d.tw, tw.data(), N * sizeof(double2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy((void*)d.twP, twP.data(), c->P * sizeof(double2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_kind, kind.data(), B * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_param, param.data(), B * sizeof(double), cudaMemcpyHostToDevice);
+  for (size_t b = 0; b < B && e == cudaSuccess; ++b)
+    if (kernels[b].kind == DA_KERNEL_TABLE)
+      e = cudaMemcpy(d_table + b * N * (N / 2 + 1), kernels[b].table, N * (N / 2 + 1) * sizeof(double),
+                     cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(d.obs, 0, B * c->nt * P2 * 2 * sizeof(double));
+  if (e == cudaSuccess) e = ops->setup();
+  if (e != cudaSuccess) {
+    g_create_error = std::string("setup: ") + cudaGetErrorString(e);
+    da_destroy(c);
+    return DA_ECUDA;
+  }
+  ops->make_mult(d, (double*)d.mult, d_kind, d_param, d_table, nu, 0);
+  c->launches++;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  std::vector<double> mult(comp);
+  if (e == cudaSuccess) e = cudaMemcpy(mult.data(), d.mult, comp * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("kernel table: ") + cudaGetErrorString(e);
+    da_destroy(c);
+    return DA_ECUDA;
+  }
+  for (double m : mult)
+    if (!std::isfinite(m) || m < 0.0) {
+      g_create_error = "kernel W is not finite and non-negative on the retained set";
+      da_destroy(c);
+      return DA_EINVAL;
+    }
+  *out = c;
+  return DA_OK;
+}
+
+extern "C" da_status da_time_kernels(da_ctx* c, int kernel_class) {
+  if (!c || kernel_class < 0 || kernel_class > 4) return fail(c, DA_EINVAL, "kernel_class must be in [0, 4]");
+  c->timed_class = kernel_class;
+  c->ev_used = 0;
+  return DA_OK;
+}
+
+extern "C" da_status da_kernel_time(da_ctx* c, double* total_ms, unsigned long long* launches) {
+  if (!c || !total_ms || !launches) return fail(c, DA_EINVAL, "arguments must not be NULL");
+  double tot = 0.0;
+  if (c->ev_used) DA_TRY_CUDA(c, cudaEventSynchronize(c->ev[c->ev_used - 1]));
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    DA_TRY_CUDA(c, cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+    tot += ms;
+  }
+  *total_ms = tot;
+  *launches = c->ev_used / 2;
+  c->ev_used = 0;
+  return DA_OK;
+}
+
+extern "C" void da_destroy(da_ctx* c) {
+  if (!c) return;
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+extern "C" const char* da_last_error(const da_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+extern "C" int da_num_obs_times(const da_ctx* c) { return c ? c->nt : 0; }
+extern "C" unsigned long long da_device_bytes(const da_ctx* c) { return c ? c->bytes : 0; }
+extern "C" unsigned long long da_launch_count(const da_ctx* c) { return c ? c->launches : 0; }
+
+extern "C" da_status da_set_observations(da_ctx* c, const double* m, void* stream) {
+  if (!c || !m) return fail(c, DA_EINVAL, "ctx and m must not be NULL");
+  const size_t bytes = (size_t)c->B * c->nt * c->P * c->P * 2 * sizeof(double);
+  DA_TRY_CUDA(c, cudaMemcpyAsync((void*)c->dev.mobs, m, bytes, cudaMemcpyDefault, (cudaStream_t)stream));
+  c->have_obs = true;
+  return DA_OK;
+}
+
+// Forward window from control s.  store: keep stage fields for the adjoint;
+// gather: fill the model observations.
+static da_status run_forward(da_ctx* c, const double* s, bool store, bool gather, cudaStream_t st) {
+  const Ops* o = c->ops;
+  const Dev& d = c->dev;
+  o->r2c_rows(d, s, st);
+  o->ctrl_cols(d, 0, st);
+  da_status r = check_launch(c, 2);
+  if (r) return r;
+  for (int k = 0; k < c->nsteps; ++k) {
+    const int obs_flag = (gather && obs_slot_host(c, k) >= 0) ? da::F_OBS : 0;
+    for (int j = 1; j <= 4; ++j) {
+      {
+        Timed t(c, 1, st);
+        o->fwd_rows(d, k, j, (store ? da::F_STORE : 0) | (j == 1 ? obs_flag : 0), st);
+      }
+      Timed t(c, 2, st);
+      o->fwd_cols(d, j, 0, st);
+    }
+    if ((r = check_launch(c, 8))) return r;
+  }
+  if (gather && obs_slot_host(c, c->nsteps) >= 0) {
+    o->fwd_rows(d, c->nsteps, 1, da::F_OBS_ONLY, st);
+    if ((r = check_launch(c))) return r;
+  }
+  return DA_OK;
+}
+
+// Backward sweep from the state in LamBar/KB/Mn (set by adj_init).
+static da_status run_adjoint(da_ctx* c, bool sources, cudaStream_t st) {
+  const Ops* o = c->ops;
+  const Dev& d = c->dev;
+  da_status r;
+  for (int k = c->nsteps - 1; k >= 0; --k) {
+    for (int j = 4; j >= 1; --j) {
+      int flags = 0;
+      if (j == 1 && sources && obs_slot_host(c, k) >= 0) flags |= da::F_SRC;
+      if (j == 1 && k == 0) flags |= da::F_FINAL;
+      {
+        Timed t(c, 3, st);
+        o->adj_rows(d, k, j, st);
+      }
+      Timed t(c, 4, st);
+      o->adj_cols(d, k, j, flags, st);
+    }
+    if ((r = check_launch(c, 8))) return r;
+  }
+  return DA_OK;
+}
+
+static da_status copy_scalars_out(da_ctx* c, double* J, cudaStream_t st) {
+  if (!J) return DA_OK;
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, J);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    at.type = cudaMemoryTypeUnregistered;
+  }
+  const bool dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  DA_TRY_CUDA(c, cudaMemcpyAsync(J, c->dev.J, c->B * sizeof(double), cudaMemcpyDefault, st));
+  if (!dev) DA_TRY_CUDA(c, cudaStreamSynchronize(st));
+  return DA_OK;
+}
+
+extern "C" da_status da_forward(da_ctx* c, const double* s, double* omegaT, double* obs, void* stream) {
+  if (!c || !s) return fail(c, DA_EINVAL, "ctx and s must not be NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  da_status r = run_forward(c, s, false, obs != nullptr, st);
+  if (r) return r;
+  if (omegaT) {
+    c->ops->compact_to_half(c->dev, c->dev.W, (double2*)omegaT, st);
+    if ((r = check_launch(c))) return r;
+  }
+  if (obs)
+    DA_TRY_CUDA(c, cudaMemcpyAsync(obs, c->dev.obs, (size_t)c->B * c->nt * c->P * c->P * 2 * sizeof(double),
+                                   cudaMemcpyDefault, st));
+  return DA_OK;
+}
+
+static da_status gradient_out(da_ctx* c, double* grad_s, cudaStream_t st) {
+  if (!grad_s) return DA_OK;
+  c->ops->spec_to_mixed(c->dev, c->dev.LamBar, da::M_CTRL, st);
+  c->ops->c2r_rows(c->dev, grad_s, st);
+  return check_launch(c, 2);
+}
+
+extern "C" da_status da_cost_grad(da_ctx* c, const double* s, double* J, double* grad_s, void* stream) {
+  if (!c || !s) return fail(c, DA_EINVAL, "ctx and s must not be NULL");
+  if (!c->have_obs) return fail(c, DA_EINVAL, "no observations: call da_set_observations first");
+  if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
+  cudaStream_t st = (cudaStream_t)stream;
+  da_status r = run_forward(c, s, true, true, st);
+  if (r) return r;
+  da::k_residual<<<c->B, 256, 0, st>>>(c->dev);
+  c->ops->adj_init(c->dev, 0, st);
+  if ((r = check_launch(c, 2))) return r;
+  if ((r = run_adjoint(c, true, st))) return r;
+  c->have_adj = true;
+  if ((r = gradient_out(c, grad_s, st))) return r;
+  return copy_scalars_out(c, J, st);
+}
+
+extern "C" da_status da_adjoint_terminal(da_ctx* c, const double* s, const double* lamT, double* grad_s, void* stream) {
+  if (!c || !s || !lamT) return fail(c, DA_EINVAL, "ctx, s and lamT must not be NULL");
+  if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
+  cudaStream_t st = (cudaStream_t)stream;
+  da_status r = run_forward(c, s, true, false, st);
+  if (r) return r;
+  c->ops->half_to_compact(c->dev, (const double2*)lamT, c->dev.LamBar, st);
+  c->ops->adj_init(c->dev, 1, st);
+  if ((r = check_launch(c, 2))) return r;
+  if ((r = run_adjoint(c, false, st))) return r;
+  c->have_adj = true;
+  return gradient_out(c, grad_s, st);
+}
+
+extern "C" da_status da_last_adjoint(da_ctx* c, double* lam0, double* filtered, void* stream) {
+  if (!c) return fail(c, DA_EINVAL, "ctx must not be NULL");
+  if (!c->have_adj) return fail(c, DA_EINVAL, "no adjoint has been run on this context");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (lam0) c->ops->compact_to_half(c->dev, c->dev.LamBar, (double2*)lam0, st);
+  if (filtered) {
+    c->ops->spec_to_mixed(c->dev, c->dev.LamBar, da::M_FILTERED, st);
+    c->ops->c2r_rows(c->dev, filtered, st);
+  }
+  return check_launch(c, (lam0 ? 1 : 0) + (filtered ? 2 : 0));
+}
+
+extern "C" da_status da_omega_from_control(da_ctx* c, const double* s, double* omega0, void* stream) {
+  if (!c || !s || !omega0) return fail(c, DA_EINVAL, "arguments must not be NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  c->ops->r2c_rows(c->dev, s, st);
+  c->ops->ctrl_cols(c->dev, da::F_NO_NEXT, st);
+  c->ops->compact_to_half(c->dev, c->dev.W, (double2*)omega0, st);
+  return check_launch(c, 3);
+}
+
+extern "C" da_status da_control_from_omega(da_ctx* c, const double* omega0, double* s, void* stream) {
+  if (!c || !s || !omega0) return fail(c, DA_EINVAL, "arguments must not be NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  c->ops->half_to_compact(c->dev, (const double2*)omega0, c->dev.Y, st);
+  c->ops->spec_to_mixed(c->dev, c->dev.Y, da::M_INV_CTRL, st);
+  c->ops->c2r_rows(c->dev, s, st);
+  return check_launch(c, 3);
+}
+
+// ---------------------------------------------------------------------------
+// L-BFGS driver (Sec. II.C: L-BFGS on the transformed control in the
+// Euclidean metric).  Members advance in lockstep: every cost-gradient
+// evaluation serves all members, and a member that is not searching
+// re-evaluates its accepted point, which changes nothing.  Each member keeps
+// a ring of memory+1 vector slots for its (s, y) pairs, so a new pair can be
+// formed and tested before the oldest one is dropped.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Vec {
+  da_ctx* c;
+  cudaStream_t st;
+  size_t len;
+
+  // out[b] = a_b . x_b (NULL pointer: 0)
+  da_status dot(const std::vector<const double*>& a, const std::vector<const double*>& x, std::vector<double>& out) {
+    const int B = c->B;
+    std::vector<const double*> ptrs(2 * B);
+    for (int b = 0; b < B; ++b) {
+      ptrs[b] = a[b];
+      ptrs[B + b] = x[b];
+    }
+    DA_TRY_CUDA(c, cudaMemcpyAsync(c->ptrs, ptrs.data(), 2 * B * sizeof(void*), cudaMemcpyHostToDevice, st));
+    const int chunks = da::dot_chunks(len);
+    da::k_dot_partial<<<dim3(chunks, B), 256, 0, st>>>((const double* const*)c->ptrs,
+                                                        (const double* const*)c->ptrs + B, c->part, len);
+    da::k_dot_final<<<B, 256, 0, st>>>(c->part, c->dots, chunks);
+    da_status r = check_launch(c, 2);
+    if (r) return r;
+    out.assign(B, 0.0);
+    DA_TRY_CUDA(c, cudaMemcpyAsync(out.data(), c->dots, B * sizeof(double), cudaMemcpyDeviceToHost, st));
+    DA_TRY_CUDA(c, cudaStreamSynchronize(st));
+    return DA_OK;
+  }
+
+  // y_b = alpha_b x_b + beta_b y_b (NULL pointer: member untouched)
+  da_status axpby(const std::vector<double>& alpha, const std::vector<const double*>& x,
+                  const std::vector<double>& beta, const std::vector<double*>& y) {
+    const int B = c->B;
+    std::vector<const void*> ptrs(2 * B);
+    std::vector<double> ab(2 * B);
+    for (int b = 0; b < B; ++b) {
+      ptrs[b] = x[b];
+      ptrs[B + b] = y[b];
+      ab[b] = alpha[b];
+      ab[B + b] = beta[b];
+    }
+    DA_TRY_CUDA(c, cudaMemcpyAsync(c->ptrs, ptrs.data(), 2 * B * sizeof(void*), cudaMemcpyHostToDevice, st));
+    DA_TRY_CUDA(c, cudaMemcpyAsync(c->scal, ab.data(), 2 * B * sizeof(double), cudaMemcpyHostToDevice, st));
+    da::k_axpby<<<dim3((unsigned)((len + 1023) / 1024), B), 256, 0, st>>>(
+        (const double* const*)c->ptrs, (double* const*)c->ptrs + B, c->scal, c->scal + B, len);
+    da_status r = check_launch(c);
+    if (r) return r;
+    DA_TRY_CUDA(c, cudaStreamSynchronize(st));  // host arrays must outlive the copies
+    return DA_OK;
+  }
+
+  double* member(double* base, int b) const { return base + (size_t)b * len; }
+};
+
+struct Member {
+  std::vector<int> pairs;    // slot indices, oldest first (at most `memory`)
+  std::vector<double> rho;   // 1 / (s . y) per pair
+  double f = 0, gnorm = 0, g0norm = 0;
+  int state = 0;             // 0 active, 1 converged, 2 line-search failure, 3 diverged
+  int iters = 0;
+};
+
+}  // namespace
+
+extern "C" da_status da_assimilate(da_ctx* c, double* s, int max_iter, const da_lbfgs_opts* opts, double* J_hist,
+                                   int* iters_done, void* stream) {
+  if (!c || !s || !J_hist || !iters_done || max_iter < 0) return fail(c, DA_EINVAL, "bad arguments");
+  if (!c->have_obs) return fail(c, DA_EINVAL, "no observations: call da_set_observations first");
+  if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
+  cudaStream_t st = (cudaStream_t)stream;
+  da_lbfgs_opts o{10, 1e-4, 0.9, 1e-10, 20};
+  if (opts) {
+    if (opts->memory > 0) o.memory = opts->memory;
+    if (opts->c1 > 0) o.c1 = opts->c1;
+    if (opts->c2 > 0) o.c2 = opts->c2;
+    if (opts->gtol_rel > 0) o.gtol_rel = opts->gtol_rel;
+    if (opts->max_ls_evals > 0) o.max_ls_evals = opts->max_ls_evals;
+  }
+  const int B = c->B, m = o.memory, slots = m + 1;
+  const size_t len = (size_t)c->n * c->n;
+  da_status r = DA_OK;
+  if (c->mem != m) {
+    if (c->mem) return fail(c, DA_EINVAL, "memory must stay the same across calls on one context");
+    auto A = [&](da_status x) {
+      if (r == DA_OK) r = x;
+    };
+    A(dalloc(c, &c->x, B * len));
+    A(dalloc(c, &c->g, B * len));
+    A(dalloc(c, &c->d, B * len));
+    A(dalloc(c, &c->xt, B * len));
+    A(dalloc(c, &c->gt, B * len));
+    A(dalloc(c, &c->S, (size_t)slots * B * len));
+    A(dalloc(c, &c->Y, (size_t)slots * B * len));
+    A(dalloc(c, &c->part, (size_t)B * da::dot_chunks(len)));
+    A(dalloc(c, &c->dots, (size_t)B));
+    A(dalloc(c, &c->scal, (size_t)2 * B));
+    A(dalloc<void*>(c, &c->ptrs, (size_t)2 * B));
+    if (r) return r;
+    c->mem = m;
+  }
+  Vec V{c, st, len};
+  auto Sslot = [&](int slot, int b) { return c->S + ((size_t)slot * B + b) * len; };
+  auto Yslot = [&](int slot, int b) { return c->Y + ((size_t)slot * B + b) * len; };
+  const std::vector<double> zeros(B, 0.0), ones(B, 1.0);
+  std::vector<Member> mb(B);
+  std::vector<double> f(B), tmp;
+  std::vector<const double*> pa(B), pb(B);
+  std::vector<double*> py(B);
+
+  DA_TRY_CUDA(c, cudaMemcpyAsync(c->x, s, B * len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if ((r = da_cost_grad(c, c->x, f.data(), c->g, st))) return r;
+  for (int b = 0; b < B; ++b) pa[b] = V.member(c->g, b);
+  if ((r = V.dot(pa, pa, tmp))) return r;
+  for (int b = 0; b < B; ++b) {
+    mb[b].f = f[b];
+    mb[b].g0norm = mb[b].gnorm = std::sqrt(tmp[b]);
+    if (!std::isfinite(f[b]) || !std::isfinite(tmp[b])) mb[b].state = 3;
+    J_hist[(size_t)b * (max_iter + 1)] = f[b];
+  }
+
+  for (int it = 0; it < max_iter; ++it) {
+    bool any = false;
+    for (int b = 0; b < B; ++b) {
+      if (mb[b].state == 0 && mb[b].gnorm <= o.gtol_rel * mb[b].g0norm) mb[b].state = 1;
+      any |= mb[b].state == 0;
+    }
+    if (!any) break;
+    auto active = [&](int b) { return mb[b].state == 0; };
+
+    // d = -H g by the two-loop recursion (d carries -q)
+    for (int b = 0; b < B; ++b) {
+      pa[b] = active(b) ? V.member(c->g, b) : nullptr;
+      py[b] = active(b) ? V.member(c->d, b) : nullptr;
+    }
+    std::vector<double> minus(B, -1.0);
+    if ((r = V.axpby(minus, pa, zeros, py))) return r;
+    int hmax = 0;
+    for (int b = 0; b < B; ++b)
+      if (active(b)) hmax = std::max(hmax, (int)mb[b].pairs.size());
+    std::vector<std::vector<double>> alpha(B, std::vector<double>(hmax, 0.0));
+    for (int h = 0; h < hmax; ++h) {  // newest to oldest
+      for (int b = 0; b < B; ++b) {
+        const int cnt = (int)mb[b].pairs.size();
+        const bool use = active(b) && h < cnt;
+        pa[b] = use ? Sslot(mb[b].pairs[cnt - 1 - h], b) : nullptr;
+        pb[b] = use ? V.member(c->d, b) : nullptr;
+      }
+      if ((r = V.dot(pa, pb, tmp))) return r;
+      std::vector<double> al(B, 0.0);
+      for (int b = 0; b < B; ++b) {
+        const int cnt = (int)mb[b].pairs.size();
+        const bool use = active(b) && h < cnt;
+        if (use) al[b] = alpha[b][h] = -mb[b].rho[cnt - 1 - h] * tmp[b];  // rho s.q
+        pa[b] = use ? Yslot(mb[b].pairs[cnt - 1 - h], b) : nullptr;
+        py[b] = use ? V.member(c->d, b) : nullptr;
+      }
+      if ((r = V.axpby(al, pa, ones, py))) return r;  // q -= alpha y
+    }
+    if (hmax > 0) {  // H0 = (s.y / y.y) I from the newest pair
+      for (int b = 0; b < B; ++b) {
+        const bool use = active(b) && !mb[b].pairs.empty();
+        pa[b] = use ? Yslot(mb[b].pairs.back(), b) : nullptr;
+      }
+      if ((r = V.dot(pa, pa, tmp))) return r;
+      std::vector<double> gam(B, 1.0);
+      for (int b = 0; b < B; ++b) {
+        const bool use = active(b) && !mb[b].pairs.empty();
+        if (use) gam[b] = 1.0 / (mb[b].rho.back() * tmp[b]);
+        pa[b] = use ? V.member(c->d, b) : nullptr;
+        py[b] = use ? V.member(c->d, b) : nullptr;
+      }
+      if ((r = V.axpby(zeros, pa, gam, py))) return r;
+    }
+    for (int h = hmax - 1; h >= 0; --h) {  // oldest to newest
+      for (int b = 0; b < B; ++b) {
+        const int cnt = (int)mb[b].pairs.size();
+        const bool use = active(b) && h < cnt;
+        pa[b] = use ? Yslot(mb[b].pairs[cnt - 1 - h], b) : nullptr;
+        pb[b] = use ? V.member(c->d, b) : nullptr;
+      }
+      if ((r = V.dot(pa, pb, tmp))) return r;
+      std::vector<double> al(B, 0.0);
+      for (int b = 0; b < B; ++b) {
+        const int cnt = (int)mb[b].pairs.size();
+        const bool use = active(b) && h < cnt;
+        if (use) al[b] = -(alpha[b][h] - (-mb[b].rho[cnt - 1 - h] * tmp[b]));  // r += (alpha - beta) s
+        pa[b] = use ? Sslot(mb[b].pairs[cnt - 1 - h], b) : nullptr;
+        py[b] = use ? V.member(c->d, b) : nullptr;
+      }
+      if ((r = V.axpby(al, pa, ones, py))) return r;
+    }
+    for (int b = 0; b < B; ++b) {
+      pa[b] = active(b) ? V.member(c->g, b) : nullptr;
+      pb[b] = active(b) ? V.member(c->d, b) : nullptr;
+    }
+    std::vector<double> gd;
+    if ((r = V.dot(pa, pb, gd))) return r;
+    {
+      std::vector<double> al(B, 0.0);
+      bool reset = false;
+      for (int b = 0; b < B; ++b) {
+        pa[b] = nullptr;
+        py[b] = nullptr;
+        if (active(b) && !(gd[b] < 0.0)) {  // not a descent direction: restart from -g
+          mb[b].pairs.clear();
+          mb[b].rho.clear();
+          al[b] = -1.0;
+          pa[b] = V.member(c->g, b);
+          py[b] = V.member(c->d, b);
+          gd[b] = -mb[b].gnorm * mb[b].gnorm;
+          reset = true;
+        }
+      }
+      if (reset && (r = V.axpby(al, pa, zeros, py))) return r;
+    }
+
+    // line search, all searching members together
+    std::vector<da::MoreThuente> ls(B);
+    std::vector<int> searching(B, 0);
+    for (int b = 0; b < B; ++b) {
+      if (!active(b)) continue;
+      const double s0 = it == 0 ? std::min(1.0, 1.0 / mb[b].gnorm) : 1.0;
+      ls[b].start(mb[b].f, gd[b], s0, o.c1, o.c2, 1e-10, 1e-20, 1e20, o.max_ls_evals);
+      searching[b] = 1;
+    }
+    std::vector<double> ft(B), dg;
+    for (;;) {
+      bool anys = false;
+      for (int b = 0; b < B; ++b) anys |= searching[b] != 0;
+      if (!anys) break;
+      // xt = x + stp d for searching members, x otherwise
+      DA_TRY_CUDA(c, cudaMemcpyAsync(c->xt, c->x, B * len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      std::vector<double> al(B, 0.0);
+      for (int b = 0; b < B; ++b) {
+        al[b] = searching[b] ? ls[b].stp() : 0.0;
+        pa[b] = searching[b] ? V.member(c->d, b) : nullptr;
+        py[b] = searching[b] ? V.member(c->xt, b) : nullptr;
+      }
+      if ((r = V.axpby(al, pa, ones, py))) return r;
+      if ((r = da_cost_grad(c, c->xt, ft.data(), c->gt, st))) return r;
+      for (int b = 0; b < B; ++b) {
+        pa[b] = searching[b] ? V.member(c->gt, b) : nullptr;
+        pb[b] = searching[b] ? V.member(c->d, b) : nullptr;
+      }
+      if ((r = V.dot(pa, pb, dg))) return r;
+      for (int b = 0; b < B; ++b) {
+        if (!searching[b]) continue;
+        if (!std::isfinite(ft[b]) || !std::isfinite(dg[b])) {
+          searching[b] = 0;
+          mb[b].state = 3;
+          continue;
+        }
+        const int act = ls[b].step(ft[b], dg[b]);
+        if (act == da::MoreThuente::EVALUATE) continue;
+        searching[b] = 0;
+        const bool ok = act == da::MoreThuente::CONVERGED;
+        if (ok || ft[b] < mb[b].f) {
+          // accept: new pair in a free slot, s = xt - x, y = gt - g
+          int freeslot = 0;
+          for (int t = 0; t < slots; ++t)
+            if (std::find(mb[b].pairs.begin(), mb[b].pairs.end(), t) == mb[b].pairs.end()) {
+              freeslot = t;
+              break;
+            }
+          double* Sd = Sslot(freeslot, b);
+          double* Yd = Yslot(freeslot, b);
+          DA_TRY_CUDA(c, cudaMemcpyAsync(Sd, V.member(c->xt, b), len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+          DA_TRY_CUDA(c, cudaMemcpyAsync(Yd, V.member(c->gt, b), len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+          std::vector<double> neg(B, 0.0);
+          std::vector<const double*> xs(B, nullptr);
+          std::vector<double*> ys(B, nullptr);
+          neg[b] = -1.0;
+          xs[b] = V.member(c->x, b);
+          ys[b] = Sd;
+          if ((r = V.axpby(neg, xs, ones, ys))) return r;
+          xs[b] = V.member(c->g, b);
+          ys[b] = Yd;
+          if ((r = V.axpby(neg, xs, ones, ys))) return r;
+          std::vector<const double*> sa(B, nullptr), ya(B, nullptr);
+          sa[b] = Sd;
+          ya[b] = Yd;
+          std::vector<double> sy, yy;
+          if ((r = V.dot(sa, ya, sy))) return r;
+          if ((r = V.dot(ya, ya, yy))) return r;
+          if (sy[b] > 1e-16 * yy[b]) {
+            if ((int)mb[b].pairs.size() == m) {
+              mb[b].pairs.erase(mb[b].pairs.begin());
+              mb[b].rho.erase(mb[b].rho.begin());
+            }
+            mb[b].pairs.push_back(freeslot);
+            mb[b].rho.push_back(1.0 / sy[b]);
+          }
+          DA_TRY_CUDA(c, cudaMemcpyAsync(V.member(c->x, b), V.member(c->xt, b), len * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, st));
+          DA_TRY_CUDA(c, cudaMemcpyAsync(V.member(c->g, b), V.member(c->gt, b), len * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, st));
+          mb[b].f = ft[b];
+          mb[b].iters = it + 1;
+          J_hist[(size_t)b * (max_iter + 1) + it + 1] = ft[b];
+        }
+        if (!ok) mb[b].state = 2;
+      }
+    }
+    for (int b = 0; b < B; ++b) pa[b] = V.member(c->g, b);
+    if ((r = V.dot(pa, pa, tmp))) return r;
+    for (int b = 0; b < B; ++b) mb[b].gnorm = std::sqrt(tmp[b]);
+  }
+  bool diverged = false, failed = false;
+  for (int b = 0; b < B; ++b) {
+    iters_done[b] = mb[b].iters;
+    for (int it = mb[b].iters + 1; it <= max_iter; ++it) J_hist[(size_t)b * (max_iter + 1) + it] = mb[b].f;
+    diverged |= mb[b].state == 3;
+    failed |= mb[b].state == 2;
+  }
+  DA_TRY_CUDA(c, cudaMemcpyAsync(s, c->x, B * len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  DA_TRY_CUDA(c, cudaStreamSynchronize(st));
+  if (diverged) return fail(c, DA_EDIVERGED, "non-finite cost or gradient");
+  if (failed) return fail(c, DA_ENOTCONV, "line search failed (step-size collapse)");
+  return DA_OK;
+}

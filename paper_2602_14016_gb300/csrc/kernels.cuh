@@ -1,0 +1,606 @@
+// kernels.cuh -- pass kernels of the cost-and-gradient evaluation.
+//
+// Layout (per member b of a batch):
+//   compact spectra  [Kr][Kc] complex: the retained set of the 2/3 rule,
+//                    kx = 0..K (columns), compact row r -> ky = r (r <= K)
+//                    or r - Kr; K = floor((N-1)/3), Kc = K+1, Kr = 2K+1.
+//   mixed fields     [N][Kc] complex: physical y, spectral kx (the transform
+//                    along y of a compact column).
+//   stage fields     [nsteps][4 stages][4 fields][N][N] double: u, v,
+//                    dw/dx, dw/dy of every RK stage state, written by the
+//                    forward row pass and read back by the adjoint row pass.
+//
+// A forward RK stage is two kernels: a ROW pass (inverse transforms along x
+// of the packed mixed rows -> u, v, w_x, w_y; stage-field store; probe
+// gather; product u w_x + v w_y; forward transform along x of two rows
+// packed as one complex sequence) and a COLUMN pass (forward transform along
+// y of the product, RK epilogue with viscosity, forcing and the stage
+// update, then the four inverse column transforms of the next stage's
+// velocity and vorticity gradient).  The adjoint mirrors this with the
+// transposed operators.  Every transform is an FP64 shared-memory FFT from
+// fft.cuh; the 1/N^2 of the inverse 2D transform is applied once, to the
+// spectral coefficients before the column transform.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+
+namespace da {
+
+enum : int {
+  F_STORE = 1,     // forward row pass: write stage fields
+  F_OBS = 2,       // forward row pass: gather probes into the observation slot
+  F_OBS_ONLY = 4,  // forward row pass: only gather probes (final state)
+  F_NO_NEXT = 8,   // column pass: skip the inverse transforms of the next stage
+  F_SRC = 16,      // adjoint column pass: add the observation source at this step
+  F_FINAL = 32     // adjoint column pass: last step (lambda_0 stays in LamBar)
+};
+
+// Multipliers of the generic spectral-to-mixed column pass.
+enum : int { M_ONE = 0, M_CTRL = 1, M_FILTERED = 2, M_INV_CTRL = 3 };
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+  int B, nsteps, every, include_t0, px, nt;
+  double dt, nu;
+  int force;
+  double amp;
+  int nf;
+  double2 *W, *Acc, *Y, *KB, *LamBar, *Sum;  // compact [B][Kr][Kc]
+  double2* Mx;                               // mixed [B][4][N][Kc]
+  double2* Mn;                               // mixed [B][N][Kc]
+  double* traj;                              // [B][nsteps][4][4][N][N]
+  double* obs;                               // model observations [B][nt][P2][2]
+  const double* mobs;                        // data [B][nt][P2][2]
+  double* res;                               // residuals [B][nt][P2][2]
+  double* J;                                 // [B]
+  const double* mult;                        // control multiplier |k| W^1/2, [B][Kr][Kc]
+  const double2* tw;                         // W_N^t, t < N
+  const double2* twP;                        // W_P^t, t < P
+};
+
+template <int N>
+struct Geo {
+  static constexpr int K = (N - 1) / 3;
+  static constexpr int Kc = K + 1;
+  static constexpr int Kr = 2 * K + 1;
+  static constexpr int NH = N / 2 + 1;
+  static constexpr int RMAX = Plan<N>::R1 > Plan<N>::R2 ? (Plan<N>::R1 > Plan<N>::R3 ? Plan<N>::R1 : Plan<N>::R3)
+                                                         : (Plan<N>::R2 > Plan<N>::R3 ? Plan<N>::R2 : Plan<N>::R3);
+  // threads: four transforms at a time, one butterfly of the widest stage each
+  static constexpr int THREADS = (4 * N / RMAX) < 32 ? 32 : 4 * N / RMAX;
+  // shared memory: twiddles + two buffers of four sequences + probe sums
+  static constexpr int PMAX = 64;
+  static constexpr size_t SMEM = sizeof(double2) * (N + 8 * N + 2 * PMAX);
+};
+
+__device__ __forceinline__ int ky_of_row(int r, int K) { return r <= K ? r : r - (2 * K + 1); }
+
+template <int N>
+__device__ __forceinline__ void load_twiddles(double2* tw, const double2* __restrict__ g) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g[i];
+}
+
+// Observation slot of step k, or -1.
+__device__ __forceinline__ int obs_slot(const Dev& d, int k) {
+  if (k == 0) return d.include_t0 ? 0 : -1;
+  if (k % d.every) return -1;
+  return k / d.every - 1 + (d.include_t0 ? 1 : 0);
+}
+
+// Full-length sequence whose inverse transform is a + i b, for two real rows
+// a, b given by their mixed half spectra A, B (kx = 0..K): Z(kx) = A + iB,
+// Z(-kx) = conj(A) + i conj(B); the DC bin keeps real parts only.
+template <int N>
+__device__ __forceinline__ double2 pack_pair(const double2* __restrict__ A, const double2* __restrict__ Bv, int kx) {
+  constexpr int K = Geo<N>::K;
+  if (kx == 0) return make_double2(A[0].x, Bv[0].x);
+  if (kx <= K) {
+    const double2 p = A[kx], q = Bv[kx];
+    return make_double2(p.x - q.y, p.y + q.x);
+  }
+  if (kx >= N - K) {
+    const double2 p = A[N - kx], q = Bv[N - kx];
+    return make_double2(p.x + q.y, q.x - p.y);
+  }
+  return make_double2(0.0, 0.0);
+}
+
+// The two half spectra packed in a forward transform Z of a + i b:
+// A(k) = (Z(k) + conj Z(-k))/2, B(k) = -i (Z(k) - conj Z(-k))/2.
+template <int N>
+__device__ __forceinline__ void unpack_pair(const double2* Z, int kx, double2& A, double2& Bv) {
+  const double2 zk = Z[kx], zm = Z[(N - kx) & (N - 1)];
+  const double sx = zk.x + zm.x, sy = zk.y - zm.y;
+  const double tx = zk.x - zm.x, ty = zk.y + zm.y;
+  A = make_double2(0.5 * sx, 0.5 * sy);
+  Bv = make_double2(0.5 * ty, -0.5 * tx);
+}
+
+// ---------------------------------------------------------------------------
+// Generic row transforms (control map, gradient map)
+// ---------------------------------------------------------------------------
+
+// Real rows in[b][y][x] -> mixed half rows Mn[b][y][kx], kx <= K (forward,
+// unnormalised), two rows per complex transform.  grid (N/2, B).
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::THREADS) k_r2c_rows(Dev d, const double* __restrict__ in) {
+  using G = Geo<N>;
+  extern __shared__ double2 sm[];
+  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
+  load_twiddles<N>(tw, d.tw);
+  const double* r0 = in + ((size_t)bm * N + y0) * N;
+  for (int x = threadIdx.x; x < N; x += blockDim.x) a[x] = make_double2(r0[x], r0[N + x]);
+  __syncthreads();
+  const double2* Z = fft_batch<N, -1>(a, b, 1, N, tw);
+  double2* M = d.Mn + ((size_t)bm * N + y0) * G::Kc;
+  for (int kx = threadIdx.x; kx < G::Kc; kx += blockDim.x) {
+    double2 A, Bv;
+    unpack_pair<N>(Z, kx, A, Bv);
+    M[kx] = A;
+    M[G::Kc + kx] = Bv;
+  }
+}
+
+// Mixed half rows Mn[b][y][kx] -> real rows out[b][y][x] (the inverse along
+// x; the 1/N^2 is already in Mn), two rows per complex transform.
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::THREADS) k_c2r_rows(Dev d, double* __restrict__ out) {
+  using G = Geo<N>;
+  extern __shared__ double2 sm[];
+  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
+  load_twiddles<N>(tw, d.tw);
+  const double2* M = d.Mn + ((size_t)bm * N + y0) * G::Kc;
+  for (int kx = threadIdx.x; kx < N; kx += blockDim.x) a[kx] = pack_pair<N>(M, M + G::Kc, kx);
+  __syncthreads();
+  const double2* z = fft_batch<N, +1>(a, b, 1, N, tw);
+  double* r0 = out + ((size_t)bm * N + y0) * N;
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    r0[x] = z[x].x;
+    r0[N + x] = z[x].y;
+  }
+}
+
+// Compact spectrum src[b] times a multiplier (and 1/N^2), transformed along
+// y -> mixed Mn[b].  grid (Kc, B).
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::THREADS) k_spec_to_mixed(Dev d, const double2* __restrict__ src, int mode) {
+  using G = Geo<N>;
+  extern __shared__ double2 sm[];
+  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  const int kx = blockIdx.x, bm = blockIdx.y;
+  load_twiddles<N>(tw, d.tw);
+  for (int y = threadIdx.x; y < N; y += blockDim.x) a[y] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const double s = 1.0 / ((double)N * N);
+  for (int r = threadIdx.x; r < G::Kr; r += blockDim.x) {
+    const int ky = ky_of_row(r, G::K);
+    const size_t idx = ((size_t)bm * G::Kr + r) * G::Kc + kx;
+    const double m = d.mult[idx];
+    double f;
+    if (mode == M_ONE) f = 1.0;
+    else if (mode == M_CTRL) f = m;
+    else if (mode == M_FILTERED) f = (kx == 0 && ky == 0) ? 0.0 : m * m / sqrt((double)(kx * kx + ky * ky));
+    else f = m != 0.0 ? 1.0 / m : 0.0;
+    a[ky & (N - 1)] = cscale(src[idx], f * s);
+  }
+  __syncthreads();
+  const double2* z = fft_batch<N, +1>(a, b, 1, N, tw);
+  double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
+  for (int y = threadIdx.x; y < N; y += blockDim.x) M[(size_t)y * G::Kc] = z[y];
+}
+
+// Compact <-> half-spectrum copies.  grid (ceil(N*NH/256), B), block 256.
+template <int N>
+__global__ void k_compact_to_half(const double2* __restrict__ src, double2* __restrict__ out) {
+  using G = Geo<N>;
+  const int bm = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * G::NH; i += gridDim.x * blockDim.x) {
+    const int q = i / G::NH, p = i - q * G::NH;
+    const int ky = q < N / 2 ? q : q - N;
+    double2 v = make_double2(0.0, 0.0);
+    if (p <= G::K && ky >= -G::K && ky <= G::K) {
+      const int r = ky >= 0 ? ky : ky + G::Kr;
+      v = src[((size_t)bm * G::Kr + r) * G::Kc + p];
+    }
+    out[(size_t)bm * N * G::NH + i] = v;
+  }
+}
+
+template <int N>
+__global__ void k_half_to_compact(const double2* __restrict__ in, double2* __restrict__ dst) {
+  using G = Geo<N>;
+  const int bm = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G::Kr * G::Kc; i += gridDim.x * blockDim.x) {
+    const int r = i / G::Kc, kx = i - r * G::Kc;
+    const int ky = ky_of_row(r, G::K);
+    dst[(size_t)bm * G::Kr * G::Kc + i] = in[((size_t)bm * N + (ky & (N - 1))) * G::NH + kx];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Control map and the four inverse column transforms of a stage state
+// ---------------------------------------------------------------------------
+
+// Writes the four zero-padded columns (u, v, w_x, w_y of state value Yv at
+// compact row r, column kx, scaled by 1/N^2) into seq[0..3][N].
+template <int N>
+__device__ __forceinline__ void put_stage_columns(double2* seq, int kx, int ky, double2 Yv) {
+  const double k2 = (double)(kx * kx + ky * ky);
+  const double ik2 = k2 > 0.0 ? 1.0 / k2 : 0.0;
+  const double s = 1.0 / ((double)N * N);
+  const int q = ky & (N - 1);
+  const double2 Ys = cscale(Yv, s);
+  const double a = ky * ik2, c = kx * ik2;
+  seq[q] = make_double2(-a * Ys.y, a * Ys.x);                  // u:  i ky / k^2
+  seq[N + q] = make_double2(c * Ys.y, -c * Ys.x);              // v: -i kx / k^2
+  seq[2 * N + q] = make_double2(-kx * Ys.y, kx * Ys.x);        // w_x: i kx
+  seq[3 * N + q] = make_double2(-ky * Ys.y, ky * Ys.x);        // w_y: i ky
+}
+
+template <int N>
+__device__ __forceinline__ void store_mixed4(const Dev& d, const double2* z, int bm, int kx) {
+  using G = Geo<N>;
+  double2* M = d.Mx + (size_t)bm * 4 * N * G::Kc + kx;
+  for (int u = threadIdx.x; u < 4 * N; u += blockDim.x) M[(size_t)u * G::Kc] = z[u];
+}
+
+// s_hat = forward transform along y of the mixed rows in Mn; w0 = mult s_hat
+// into W (and Y); then, unless F_NO_NEXT, the four inverse column transforms
+// of stage 1.  grid (Kc, B).
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::THREADS) k_ctrl_cols(Dev d, int flags) {
+  using G = Geo<N>;
+  extern __shared__ double2 sm[];
+  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  const int kx = blockIdx.x, bm = blockIdx.y;
+  load_twiddles<N>(tw, d.tw);
+  const double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
+  for (int y = threadIdx.x; y < N; y += blockDim.x) a[y] = M[(size_t)y * G::Kc];
+  __syncthreads();
+  double2* r = fft_batch<N, -1>(a, b, 1, N, tw);
+  double2* q = (r == a) ? b : a;
+  for (int u = threadIdx.x; u < 4 * N; u += blockDim.x) q[u] = make_double2(0.0, 0.0);
+  __syncthreads();
+  for (int rr = threadIdx.x; rr < G::Kr; rr += blockDim.x) {
+    const int ky = ky_of_row(rr, G::K);
+    const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+    const double2 w0 = cscale(r[ky & (N - 1)], d.mult[idx]);
+    d.W[idx] = w0;
+    d.Y[idx] = w0;
+    put_stage_columns<N>(q, kx, ky, w0);
+  }
+  if (flags & F_NO_NEXT) return;
+  __syncthreads();
+  const double2* z = fft_batch<N, +1>(q, r, 4, N, tw);
+  store_mixed4<N>(d, z, bm, kx);
+}
+
+// ---------------------------------------------------------------------------
+// Forward RK stage
+// ---------------------------------------------------------------------------
+
+// Row pass of stage `stage` (1..4) of step n.  grid (N/2, B).
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_rows(Dev d, int n, int stage, int flags) {
+  using G = Geo<N>;
+  extern __shared__ double2 sm[];
+  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
+  load_twiddles<N>(tw, d.tw);
+  const double2* M = d.Mx + (size_t)bm * 4 * N * G::Kc;
+  // sequence 2*rr + g packs row y0+rr of fields (2g, 2g+1): (u, v) or (w_x, w_y)
+  for (int u = threadIdx.x; u < 4 * N; u += blockDim.x) {
+    const int seq = u / N, kx = u - seq * N;
+    const int rr = seq >> 1, g = seq & 1;
+    const double2* A = M + ((size_t)(2 * g) * N + y0 + rr) * G::Kc;
+    const double2* Bv = M + ((size_t)(2 * g + 1) * N + y0 + rr) * G::Kc;
+    a[u] = pack_pair<N>(A, Bv, kx);
+  }
+  __syncthreads();
+  const double2* r = fft_batch<N, +1>(a, b, 4, N, tw);
+  double2* q = (r == a) ? b : a;
+  const int st = N / d.px;
+  const int slot = (flags & (F_OBS | F_OBS_ONLY)) ? obs_slot(d, n) : -1;
+  double* trj = (flags & F_STORE)
+                    ? d.traj + (((size_t)bm * d.nsteps + n) * 4 + (stage - 1)) * 4 * (size_t)N * N
+                    : nullptr;
+  for (int u = threadIdx.x; u < 2 * N; u += blockDim.x) {
+    const int rr = u / N, x = u - rr * N, y = y0 + rr;
+    const double2 uv = r[(2 * rr) * N + x], wg = r[(2 * rr + 1) * N + x];
+    if (trj) {
+      const size_t o = (size_t)y * N + x;
+      trj[o] = uv.x;
+      trj[(size_t)N * N + o] = uv.y;
+      trj[(size_t)2 * N * N + o] = wg.x;
+      trj[(size_t)3 * N * N + o] = wg.y;
+    }
+    if (slot >= 0 && (y % st) == 0 && (x % st) == 0) {
+      const int p = (y / st) * d.px + x / st;
+      double* o = d.obs + (((size_t)bm * d.nt + slot) * d.px * d.px + p) * 2;
+      o[0] = uv.x;
+      o[1] = uv.y;
+    }
+    reinterpret_cast<double*>(q)[2 * x + rr] = fma(uv.x, wg.x, uv.y * wg.y);
+  }
+  if (flags & F_OBS_ONLY) return;
+  __syncthreads();
+  const double2* Z = fft_batch<N, -1>(q, const_cast<double2*>(r), 1, N, tw);
+  double2* O = d.Mn + ((size_t)bm * N + y0) * G::Kc;
+  for (int kx = threadIdx.x; kx < G::Kc; kx += blockDim.x) {
+    double2 A, Bv;
+    unpack_pair<N>(Z, kx, A, Bv);
+    O[kx] = A;
+    O[G::Kc + kx] = Bv;
+  }
+}
+
+// Column pass of stage `stage`: k_j = -P DFT(u.grad w) - nu k^2 y_j + f_hat,
+// the RK4 update, and the inverse column transforms of the next stage
+// state.  Acc holds k1 + 2 k2 + 2 k3 (+ k4).  grid (Kc, B).
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, int flags) {
+  using G = Geo<N>;
+  extern __shared__ double2 sm[];
+  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  const int kx = blockIdx.x, bm = blockIdx.y;
+  load_twiddles<N>(tw, d.tw);
+  const double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
+  for (int y = threadIdx.x; y < N; y += blockDim.x) a[y] = M[(size_t)y * G::Kc];
+  __syncthreads();
+  double2* r = fft_batch<N, -1>(a, b, 1, N, tw);
+  double2* q = (r == a) ? b : a;
+  for (int u = threadIdx.x; u < 4 * N; u += blockDim.x) q[u] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const double dt = d.dt;
+  const double fval = -d.amp * d.nf * (double)N * N / 2.0;
+  for (int rr = threadIdx.x; rr < G::Kr; rr += blockDim.x) {
+    const int ky = ky_of_row(rr, G::K);
+    const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+    const double2 nh = r[ky & (N - 1)];
+    const double2 yv = d.Y[idx];
+    const double k2 = (double)(kx * kx + ky * ky);
+    double2 F = make_double2(-nh.x - d.nu * k2 * yv.x, -nh.y - d.nu * k2 * yv.y);
+    if (d.force && kx == 0 && (ky == d.nf || ky == -d.nf)) F.x += fval;
+    const double2 w = d.W[idx];
+    double2 ynext;
+    if (stage == 1) {
+      d.Acc[idx] = F;
+      ynext = make_double2(w.x + 0.5 * dt * F.x, w.y + 0.5 * dt * F.y);
+    } else if (stage == 2) {
+      const double2 acc = d.Acc[idx];
+      d.Acc[idx] = make_double2(acc.x + 2.0 * F.x, acc.y + 2.0 * F.y);
+      ynext = make_double2(w.x + 0.5 * dt * F.x, w.y + 0.5 * dt * F.y);
+    } else if (stage == 3) {
+      const double2 acc = d.Acc[idx];
+      d.Acc[idx] = make_double2(acc.x + 2.0 * F.x, acc.y + 2.0 * F.y);
+      ynext = make_double2(w.x + dt * F.x, w.y + dt * F.y);
+    } else {
+      const double2 acc = d.Acc[idx];
+      const double c = dt / 6.0;
+      ynext = make_double2(w.x + c * (acc.x + F.x), w.y + c * (acc.y + F.y));
+      d.W[idx] = ynext;
+    }
+    d.Y[idx] = ynext;
+    put_stage_columns<N>(q, kx, ky, ynext);
+  }
+  if (flags & F_NO_NEXT) return;
+  __syncthreads();
+  const double2* z = fft_batch<N, +1>(q, r, 4, N, tw);
+  store_mixed4<N>(d, z, bm, kx);
+}
+
+// r = model observations - data and J = 1/2 sum r^2 per member, in a fixed
+// order (deterministic).  grid B, block 256.  Defined in residual.cu.
+__global__ void k_residual(Dev d);
+
+// ---------------------------------------------------------------------------
+// Adjoint
+// ---------------------------------------------------------------------------
+
+// Separable DFT of the residual at observation slot `slot` on the probe
+// lattice: for each lattice row, T(kx) = sum_q r[row][q] W_P^{kx q}; the
+// column pass then sums over rows with W_P^{ky row}.  Fills Tu, Tv [P].
+__device__ __forceinline__ void probe_row_sums(const Dev& d, int bm, int slot, int kx, double2* Tu, double2* Tv) {
+  const int P = d.px;
+  const double* r = d.res + ((size_t)bm * d.nt + slot) * P * P * 2;
+  for (int row = threadIdx.x; row < P; row += blockDim.x) {
+    double2 su = make_double2(0.0, 0.0), sv = make_double2(0.0, 0.0);
+    for (int qq = 0; qq < P; ++qq) {
+      const double2 w = d.twP[(kx * qq) % P];
+      const double ru = r[(row * P + qq) * 2], rv = r[(row * P + qq) * 2 + 1];
+      su = make_double2(fma(ru, w.x, su.x), fma(ru, w.y, su.y));
+      sv = make_double2(fma(rv, w.x, sv.x), fma(rv, w.y, sv.y));
+    }
+    Tu[row] = su;
+    Tv[row] = sv;
+  }
+}
+
+// H^T r at (kx, ky): (-i ky/k^2) R_u + (i kx/k^2) R_v with R the DFT of the
+// probe residual scattered onto the grid.
+__device__ __forceinline__ double2 probe_source(const Dev& d, int kx, int ky, const double2* Tu, const double2* Tv) {
+  const int P = d.px;
+  double2 Ru = make_double2(0.0, 0.0), Rv = make_double2(0.0, 0.0);
+  const int kyp = ((ky % P) + P) % P;
+  for (int row = 0; row < P; ++row) {
+    const double2 w = d.twP[(kyp * row) % P];
+    Ru = cadd(Ru, cmul(Tu[row], w));
+    Rv = cadd(Rv, cmul(Tv[row], w));
+  }
+  const double k2 = (double)(kx * kx + ky * ky);
+  const double ik2 = k2 > 0.0 ? 1.0 / k2 : 0.0;
+  const double a = ky * ik2, c = kx * ik2;
+  // (-i a) Ru + (i c) Rv
+  return make_double2(a * Ru.y - c * Rv.y, -a * Ru.x + c * Rv.x);
+}
+
+// Start of the adjoint sweep: LamBar = H^T r at the last step (or, with
+// from_lambar, the terminal field already in LamBar), KB = dt/6 LamBar and
+// its inverse column transform into Mn.  grid (Kc, B).
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_init(Dev d, int from_lambar) {
+  using G = Geo<N>;
+  extern __shared__ double2 sm[];
+  double2 *tw = sm, *a = tw + N, *b = a + 4 * N, *Tu = b + 4 * N, *Tv = Tu + G::PMAX;
+  const int kx = blockIdx.x, bm = blockIdx.y;
+  load_twiddles<N>(tw, d.tw);
+  const int slot = from_lambar ? -1 : obs_slot(d, d.nsteps);
+  if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
+  for (int y = threadIdx.x; y < N; y += blockDim.x) a[y] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const double s = 1.0 / ((double)N * N);
+  for (int rr = threadIdx.x; rr < G::Kr; rr += blockDim.x) {
+    const int ky = ky_of_row(rr, G::K);
+    const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+    double2 lam = from_lambar ? d.LamBar[idx] : make_double2(0.0, 0.0);
+    if (slot >= 0) lam = probe_source(d, kx, ky, Tu, Tv);
+    d.LamBar[idx] = lam;
+    const double2 kb = cscale(lam, d.dt / 6.0);
+    d.KB[idx] = kb;
+    a[ky & (N - 1)] = cscale(kb, s);
+  }
+  __syncthreads();
+  const double2* z = fft_batch<N, +1>(a, b, 1, N, tw);
+  double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
+  for (int y = threadIdx.x; y < N; y += blockDim.x) M[(size_t)y * G::Kc] = z[y];
+}
+
+// Adjoint row pass of stage `stage` of step n: mu = inverse transform along x
+// of the mixed kbar rows (two rows packed), products with the stored u, v,
+// w_x, w_y, and their forward transforms along x.  grid (N/2, B).
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_rows(Dev d, int n, int stage) {
+  using G = Geo<N>;
+  extern __shared__ double2 sm[];
+  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
+  load_twiddles<N>(tw, d.tw);
+  const double2* M = d.Mn + ((size_t)bm * N + y0) * G::Kc;
+  for (int kx = threadIdx.x; kx < N; kx += blockDim.x) a[kx] = pack_pair<N>(M, M + G::Kc, kx);
+  __syncthreads();
+  double2* r = fft_batch<N, +1>(a, b, 1, N, tw);
+  double2* q = (r == a) ? b : a;
+  const double* trj = d.traj + (((size_t)bm * d.nsteps + n) * 4 + (stage - 1)) * 4 * (size_t)N * N;
+  for (int u = threadIdx.x; u < 2 * N; u += blockDim.x) {
+    const int rr = u / N, x = u - rr * N;
+    const double mu = rr ? r[x].y : r[x].x;
+    const size_t o = (size_t)(y0 + rr) * N + x;
+    const double fu = trj[o], fv = trj[(size_t)N * N + o];
+    const double fwx = trj[(size_t)2 * N * N + o], fwy = trj[(size_t)3 * N * N + o];
+    q[(2 * rr) * N + x] = make_double2(fu * mu, fv * mu);
+    q[(2 * rr + 1) * N + x] = make_double2(fwx * mu, fwy * mu);
+  }
+  __syncthreads();
+  const double2* Z = fft_batch<N, -1>(q, r, 4, N, tw);
+  double2* O = d.Mx + (size_t)bm * 4 * N * G::Kc;
+  for (int u = threadIdx.x; u < 4 * G::Kc; u += blockDim.x) {
+    const int seq = u / G::Kc, kx = u - seq * G::Kc;
+    const int rr = seq >> 1, g = seq & 1;
+    double2 A, Bv;
+    unpack_pair<N>(Z + seq * N, kx, A, Bv);
+    O[((size_t)(2 * g) * N + y0 + rr) * G::Kc + kx] = A;
+    O[((size_t)(2 * g + 1) * N + y0 + rr) * G::Kc + kx] = Bv;
+  }
+}
+
+// Adjoint column pass of stage `stage` of step n:
+//   ybar_j = P[ i ky/k^2 D(w_x mu) - i kx/k^2 D(w_y mu) + i kx D(u mu)
+//              + i ky D(v mu) ] - nu k^2 kbar_j,
+// the transposed RK4 combination, the observation source at step n (on
+// stage 1), and the inverse column transform of the next kbar.
+// grid (Kc, B).
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int stage, int flags) {
+  using G = Geo<N>;
+  extern __shared__ double2 sm[];
+  double2 *tw = sm, *a = tw + N, *b = a + 4 * N, *Tu = b + 4 * N, *Tv = Tu + G::PMAX;
+  const int kx = blockIdx.x, bm = blockIdx.y;
+  load_twiddles<N>(tw, d.tw);
+  const double2* M = d.Mx + (size_t)bm * 4 * N * G::Kc + kx;
+  for (int u = threadIdx.x; u < 4 * N; u += blockDim.x) a[u] = M[(size_t)u * G::Kc];
+  const int slot = (flags & F_SRC) ? obs_slot(d, n) : -1;
+  if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
+  __syncthreads();
+  double2* r = fft_batch<N, -1>(a, b, 4, N, tw);
+  double2* q = (r == a) ? b : a;
+  for (int y = threadIdx.x; y < N; y += blockDim.x) q[y] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const double dt = d.dt;
+  const double s = 1.0 / ((double)N * N);
+  for (int rr = threadIdx.x; rr < G::Kr; rr += blockDim.x) {
+    const int ky = ky_of_row(rr, G::K);
+    const int qi = ky & (N - 1);
+    const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+    const double2 P1 = r[qi], P2 = r[N + qi], P3 = r[2 * N + qi], P4 = r[3 * N + qi];
+    const double k2 = (double)(kx * kx + ky * ky);
+    const double ik2 = k2 > 0.0 ? 1.0 / k2 : 0.0;
+    const double a1 = ky * ik2, c1 = kx * ik2;
+    // terms of the transposed products (conjugate symbols), subtracted in turn
+    const double2 t0 = make_double2(a1 * P3.y, -a1 * P3.x);   // (-i ky/k^2) D(w_x mu)
+    const double2 t1 = make_double2(-c1 * P4.y, c1 * P4.x);   // ( i kx/k^2) D(w_y mu)
+    const double2 t2 = make_double2(kx * P1.y, -kx * P1.x);   // (-i kx) D(u mu)
+    const double2 t3 = make_double2(ky * P2.y, -ky * P2.x);   // (-i ky) D(v mu)
+    const double2 kb = d.KB[idx];
+    double2 yb;
+    yb.x = (((-t0.x) - t1.x) - t2.x) - t3.x - d.nu * k2 * kb.x;
+    yb.y = (((-t0.y) - t1.y) - t2.y) - t3.y - d.nu * k2 * kb.y;
+    const double2 lb = d.LamBar[idx];
+    double2 nk;
+    if (stage == 4) {
+      d.Sum[idx] = yb;
+      nk = make_double2(dt / 3.0 * lb.x + dt * yb.x, dt / 3.0 * lb.y + dt * yb.y);
+    } else if (stage == 3) {
+      const double2 sm2 = d.Sum[idx];
+      d.Sum[idx] = cadd(sm2, yb);
+      nk = make_double2(dt / 3.0 * lb.x + dt / 2.0 * yb.x, dt / 3.0 * lb.y + dt / 2.0 * yb.y);
+    } else if (stage == 2) {
+      const double2 sm2 = d.Sum[idx];
+      d.Sum[idx] = cadd(sm2, yb);
+      nk = make_double2(dt / 6.0 * lb.x + dt / 2.0 * yb.x, dt / 6.0 * lb.y + dt / 2.0 * yb.y);
+    } else {
+      const double2 sum = cadd(d.Sum[idx], yb);
+      double2 lam = cadd(lb, sum);
+      if (slot >= 0) lam = cadd(lam, probe_source(d, kx, ky, Tu, Tv));
+      d.LamBar[idx] = lam;
+      nk = cscale(lam, dt / 6.0);
+    }
+    d.KB[idx] = nk;
+    q[qi] = cscale(nk, s);
+  }
+  if (flags & F_FINAL) return;
+  __syncthreads();
+  const double2* z = fft_batch<N, +1>(q, r, 1, N, tw);
+  double2* O = d.Mn + (size_t)bm * N * G::Kc + kx;
+  for (int y = threadIdx.x; y < N; y += blockDim.x) O[(size_t)y * G::Kc] = z[y];
+}
+
+// Control multipliers m(k) = |k| W(k)^{1/2} on the retained set (0 at k = 0),
+// per member.  grid (ceil(Kr*Kc/256), B), block 256.
+template <int N>
+__global__ void k_make_mult(double* __restrict__ mult, const int* __restrict__ kind, const double* __restrict__ param,
+                            const double* __restrict__ table, double nu) {
+  using G = Geo<N>;
+  const int bm = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G::Kr * G::Kc; i += gridDim.x * blockDim.x) {
+    const int r = i / G::Kc, kx = i - r * G::Kc;
+    const int ky = ky_of_row(r, G::K);
+    const double k2 = (double)(kx * kx + ky * ky);
+    const double k = sqrt(k2);
+    double W;
+    const double a = param[bm];
+    switch (kind[bm]) {
+      case 0: W = 1.0; break;
+      case 1: W = exp(-a * k); break;
+      case 2: W = pow(k, -2.0 * a); break;
+      case 3: W = exp(-nu * a * k2); break;
+      default: W = table[((size_t)bm * N + (ky & (N - 1))) * G::NH + kx]; break;
+    }
+    mult[(size_t)bm * G::Kr * G::Kc + i] = (kx == 0 && ky == 0) ? 0.0 : k * sqrt(W);
+  }
+}
+
+}  // namespace da
