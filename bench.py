@@ -1,0 +1,445 @@
+#!/usr/bin/env python
+"""Throughput of the FP64 cost-and-gradient evaluation on GB300.
+
+Workload (one "step" = one batched cost-and-gradient evaluation, the whole
+hot path): forced Kolmogorov flow on a 256^2 grid, f = (sin 4y, 0),
+nu = 1/100, spun up 50 time units (25,000 RK4 steps of 2e-3, untimed) from a
+seeded unit-energy field; window of 2000 RK4 steps of 2e-3; 16x16 velocity
+probes every 20 steps with 1 % Gaussian noise; first guess from the
+trigonometric interpolation of the t = 0 probe velocities; the seven kernels
+of the sweep |k|^(-2s), s in {0, 0.5, 1, 1.5}, and exp(-a|k|), a in
+{0.1, 0.3, 1}, evaluated together as one batch of seven members.
+
+Metric: fwd+adjoint gridpoint-steps/s (FP64) = members x n^2 x nsteps per
+evaluation / time.  The timed region holds K evaluations with the inputs
+resident on the device; the stage-field trajectory of an evaluation
+(117 GB) is far larger than L2, so no flush is needed.  `e2e` repeats the
+measurement through the public API from pinned host memory (controls in,
+cost and gradient out).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload.  Under torchrun each rank runs its
+own batch (replicas; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SWEEP = [("frac", 0.0), ("frac", 0.5), ("frac", 1.0), ("frac", 1.5), ("exp_abs", 0.1), ("exp_abs", 0.3),
+         ("exp_abs", 1.0)]
+W = dict(n=256, nsteps=2000, dt=2e-3, nu=1e-2, forcing="kolmogorov", amp=1.0, nf=4, px=16, every=20, noise=0.01,
+         spinup_steps=25000, seed=0)
+WORKLOAD_NAME = "kolmogorov-256sq-2000steps-16x16probes-7kernel-sweep"
+METRIC = "fwd+adjoint gridpoint-steps/s FP64"
+UNIT = "gridpoint-steps/s"
+
+# FP64 peak for an ALU-bound kernel: 152 SMs x 2 DFMA/clk/SM (measured by a
+# DFMA throughput probe on this GPU) x 2 flop x 2.07 GHz maximum SM clock.
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+
+# DRAM bytes per launch of each pass kernel at this workload, from one ncu
+# capture; valid only for the kernel sources they were taken from.
+TRAFFIC = {"src_hash": None}
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2602_14016_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def fft_flops(n: int) -> float:
+    """Nominal flops of one complex length-n FFT (5 n log2 n)."""
+    return 5.0 * n * np.log2(n)
+
+
+def pass_flops(n: int, batch: int) -> dict:
+    """Algorithmic FP64 flops per launch of each pass kernel (nominal FFT
+    count of the transforms it performs plus its pointwise arithmetic)."""
+    K = (n - 1) // 3
+    Kc, Kr = K + 1, 2 * K + 1
+    f = fft_flops(n)
+    return {
+        "fwd_rows": batch * (2.5 * n * f + 3.0 * n * n),
+        "fwd_cols": batch * (5.0 * Kc * f + 24.0 * Kr * Kc),
+        "adj_rows": batch * (2.5 * n * f + 4.0 * n * n),
+        "adj_cols": batch * (5.0 * Kc * f + 34.0 * Kr * Kc),
+    }
+
+
+def flops_per_gridpoint_step(n: int) -> float:
+    p = pass_flops(n, 1)
+    return 4.0 * sum(p.values()) / (n * n)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.out = out
+        return False
+
+    def summary(self):
+        if self.p is None:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "out", "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def first_guess_from_probes(w_hat: np.ndarray, n: int, px: int) -> np.ndarray:
+    """Vorticity of the trigonometric interpolation of the t = 0 probe velocities.
+
+    Input preparation on the host (numpy): u, v of the truth at the probe
+    lattice, their px x px DFT, vorticity i kx v - i ky u on the coarse
+    modes, zero-padded into the n^2 half spectrum."""
+    from paper_2602_14016_gb300 import synthetic
+
+    KX, KY = synthetic.wavenumbers(n)
+    k2 = (KX**2 + KY**2).astype(float)
+    ik2 = np.where(k2 > 0, 1.0 / np.where(k2 > 0, k2, 1.0), 0.0)
+    u = np.fft.irfft2(1j * KY * ik2 * w_hat, s=(n, n))
+    v = np.fft.irfft2(-1j * KX * ik2 * w_hat, s=(n, n))
+    st = n // px
+    uc, vc = u[::st, ::st], v[::st, ::st]
+    Uc, Vc = np.fft.rfft2(uc), np.fft.rfft2(vc)
+    kxc, kyc = np.meshgrid(np.arange(px // 2 + 1), np.fft.fftfreq(px, 1.0 / px).astype(int))
+    Wc = 1j * kxc * Vc - 1j * kyc * Uc
+    out = np.zeros((n, n // 2 + 1), complex)
+    scale = (n / px) ** 2
+    for q in range(px):
+        ky = kyc[q, 0]
+        if abs(ky) >= px // 2:
+            continue
+        for p in range(px // 2):
+            out[ky % n, p] = Wc[q, p] * scale
+    out[0, 0] = 0
+    return out
+
+
+def prepare(api, torch, kernels, device):
+    """Spin-up, truth observations with noise, first-guess controls."""
+    from paper_2602_14016_gb300 import synthetic
+
+    n, nsteps = W["n"], W["nsteps"]
+    chunk = min(2500, W["spinup_steps"]) or 1
+    spin = api.Context(api.Config(n=n, nsteps=chunk, dt=W["dt"], nu=W["nu"], forcing=W["forcing"], amp=W["amp"],
+                                  nf=W["nf"], px=W["px"], every=chunk, kernels=[api.KernelSpec("identity", 0.0)],
+                                  store=False), device)
+    w = torch.from_numpy(synthetic.random_vorticity_hat(n, W["seed"])[None]).to(device)
+    for _ in range(W["spinup_steps"] // chunk if W["spinup_steps"] else 0):
+        s0 = spin.control_from_omega(w)
+        w, _ = spin.forward(s0)
+    win = api.Context(api.Config(n=n, nsteps=nsteps, dt=W["dt"], nu=W["nu"], forcing=W["forcing"], amp=W["amp"],
+                                 nf=W["nf"], px=W["px"], every=W["every"], kernels=[api.KernelSpec("identity", 0.0)],
+                                 store=False), device)
+    s_truth = win.control_from_omega(w)
+    _, obs = win.forward(s_truth)
+    obs = obs.cpu().numpy()[0]
+    rms = float(np.sqrt(np.mean(obs**2)))
+    m = obs + W["noise"] * rms * synthetic.gaussian_draws(obs.shape, W["seed"] + 1)
+    w_truth = w.cpu().numpy()[0]
+    spin.close()
+    win.close()
+    w_guess = first_guess_from_probes(w_truth, n, W["px"])
+    B = len(kernels)
+    return np.repeat(m[None], B, 0), np.repeat(w_guess[None], B, 0), w_truth
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2602_14016_gb300 import api, build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    kernels = SWEEP
+    B = len(kernels)
+    n, nsteps = W["n"], W["nsteps"]
+    m, w_guess, _ = prepare(api, torch, kernels, device)
+    cfg = api.Config(n=n, nsteps=nsteps, dt=W["dt"], nu=W["nu"], forcing=W["forcing"], amp=W["amp"], nf=W["nf"],
+                     px=W["px"], every=W["every"], kernels=[api.KernelSpec(k, a) for k, a in kernels])
+    ctx = api.Context(cfg, device)
+    ctx.set_observations(torch.from_numpy(m).to(device))
+    s = ctx.control_from_omega(torch.from_numpy(w_guess).to(device))
+    stream = torch.cuda.current_stream()
+
+    # warm-up; with at least four, the first four also time one pass-kernel
+    # class each and the dominant class is the one timed below
+    classes = ["fwd_rows", "fwd_cols", "adj_rows", "adj_cols"]
+    class_ms = {}
+    J = None
+    for i in range(args.warmup):
+        timed = i < 4 and args.warmup >= 4
+        if timed:
+            ctx.time_kernels(classes[i])
+        J, g = ctx.cost_grad(s)
+        torch.cuda.synchronize()
+        if timed:
+            class_ms[classes[i]] = ctx.kernel_time()
+    ctx.time_kernels("off")
+    dom = args.roofline_class or (max(class_ms, key=lambda c: class_ms[c][0]) if class_ms else "adj_rows")
+    if J is None:
+        J, g = ctx.cost_grad(s)
+    Jw = J.cpu().numpy()
+    if not np.all(np.isfinite(Jw)):
+        raise RuntimeError(f"non-finite cost in warm-up: {Jw}")
+
+    # timed region: K evaluations, inputs resident
+    ctx.time_kernels(dom)
+    launches0 = ctx.launches
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")
+        ev0.record(stream)
+        for _ in range(args.steps):
+            J, g = ctx.cost_grad(s)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launches - launches0
+    dom_ms, dom_n = ctx.kernel_time()
+    ctx.time_kernels("off")
+    if world > 1:
+        t = torch.tensor([ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    units = world * B * n * n * nsteps * args.steps
+    value = units / (ms / 1e3)
+
+    # end to end through the public API from pinned host memory
+    s_host = s.cpu().pin_memory()
+    J_host = torch.empty(B, dtype=torch.float64).pin_memory()
+    g_host = torch.empty_like(s_host).pin_memory()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_steps = max(1, min(args.steps, 3))
+    e0.record(stream)
+    for _ in range(e_steps):
+        s_dev = s_host.to(device, non_blocking=True)
+        J, g = ctx.cost_grad(s_dev)
+        J_host.copy_(J, non_blocking=True)
+        g_host.copy_(g, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t.item())
+    e2e_value = world * B * n * n * nsteps * e_steps / (e_ms / 1e3)
+
+    # the plain one-job-per-launch path: the same members one at a time
+    plain = None
+    if rank == 0 and args.plain:
+        cfg1 = api.Config(n=n, nsteps=nsteps, dt=W["dt"], nu=W["nu"], forcing=W["forcing"], amp=W["amp"],
+                          nf=W["nf"], px=W["px"], every=W["every"], kernels=[api.KernelSpec(*kernels[0])])
+        del ctx
+        torch.cuda.empty_cache()
+        ctx1 = api.Context(cfg1, device)
+        ctx1.set_observations(torch.from_numpy(m[:1]).to(device))
+        s1 = [ctx1.control_from_omega(torch.from_numpy(w_guess[:1]).to(device))]
+        ctx1.cost_grad(s1[0])
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(B):
+            ctx1.cost_grad(s1[0])
+        p1.record(stream)
+        torch.cuda.synchronize()
+        p_ms = p0.elapsed_time(p1)
+        plain = {"value": B * n * n * nsteps / (p_ms / 1e3), "unit": UNIT, "ms_per_member": p_ms / B,
+                 "note": "same members evaluated one per launch sequence (batch 1)"}
+        ctx1.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    pf = pass_flops(n, B)[dom]
+    avg_ms = dom_ms / max(dom_n, 1)
+    achieved = pf / (avg_ms / 1e3) / 1e9
+    traffic = TRAFFIC.get(dom) if TRAFFIC.get("src_hash") == src_hash() else None
+    cpu = cpu_baseline(args) if args.cpu_baseline else None
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded spun-up Kolmogorov flow, noisy probe observations)",
+        "config": {"workload": WORKLOAD_NAME, "grid": n, "nsteps": nsteps, "dt": W["dt"], "nu": W["nu"],
+                   "probes": f"{W['px']}x{W['px']} every {W['every']}", "members_per_gpu": B,
+                   "kernels": [f"{k}:{a}" for k, a in kernels], "l2": "inputs larger than L2 (117 GB stage-field "
+                   "trajectory streamed per evaluation)", "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(s_host.numel() * 8),
+                "d2h_bytes_per_step": int(J_host.numel() * 8 + g_host.numel() * 8)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
+                     "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+                     "flops_per_launch": pf, "avg_launch_ms": avg_ms, "launches_timed": dom_n,
+                     "class_ms_warmup": {k: v[0] for k, v in class_ms.items()}},
+        "flops_per_gridpoint_step": flops_per_gridpoint_step(n),
+        "achieved_gflops_step": value * flops_per_gridpoint_step(n) / 1e9,
+        "cpu_baseline": cpu,
+        "plain_path": plain,
+        "clocks": clk.summary(),
+        "J_mean": float(np.mean(J.cpu().numpy())),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def oracle_sample(n_sample_steps: int):
+    """One oracle cost-and-gradient evaluation on a bounded sample of the
+    workload: the first n_sample_steps steps of the window (one observation
+    time), one member (kernel |k|^-1), same grid and physics."""
+    import oracle
+    from paper_2602_14016_gb300 import synthetic
+
+    n = W["n"]
+    P = oracle.Problem(n=n, nsteps=n_sample_steps, dt=W["dt"], nu=W["nu"], forcing=W["forcing"], amp=W["amp"],
+                       nf=W["nf"], px=W["px"], every=n_sample_steps, kernel="frac", kparam=0.5)
+    truth = oracle.control_from_omega(P, synthetic.random_vorticity_hat(n, W["seed"]))
+    guess = oracle.control_from_omega(P, synthetic.random_vorticity_hat(n, W["seed"] + 2))
+    _, m = oracle.forward(P, truth)
+    t0 = time.perf_counter()
+    J, g, _ = oracle.cost_grad(P, guess, m)
+    dt = time.perf_counter() - t0
+    return n * n * n_sample_steps / dt, dt
+
+
+def cpu_baseline(args):
+    oracle_steps = 20
+    val, secs = oracle_sample(oracle_steps)
+    return {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one cost+gradient evaluation of the first {oracle_steps} steps of the 256^2 window, one "
+                      f"member, single-threaded C oracle ({secs:.1f} s)"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    oracle_steps = 20
+    for _ in range(args.warmup):
+        oracle_sample(2)
+    total_units, total_s = 0.0, 0.0
+    for _ in range(args.steps):
+        v, s = oracle_sample(oracle_steps)
+        total_units += W["n"] ** 2 * oracle_steps
+        total_s += s
+    value = total_units / total_s
+    sample = (f"each step one cost+gradient evaluation of the first {oracle_steps} steps of the 256^2 window, one "
+              "member, single-threaded C oracle")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "grid": W["n"], "sample_steps": oracle_steps},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--window-steps", type=int, default=W["nsteps"],
+                    help="shorter window (multiple of 20) for profiling runs; the default is the workload's 2000")
+    ap.add_argument("--spinup-steps", type=int, default=W["spinup_steps"])
+    ap.add_argument("--roofline-class", default=None, choices=["fwd_rows", "fwd_cols", "adj_rows", "adj_cols"])
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-plain", dest="plain", action="store_false")
+    args = ap.parse_args()
+    if args.window_steps % W["every"]:
+        ap.error("--window-steps must be a multiple of 20")
+    W["nsteps"] = args.window_steps
+    W["spinup_steps"] = args.spinup_steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,74 @@
+"""Behaviour of the C ABI on a GPU beyond parity: error statuses, launch
+accounting, kernel timing, determinism."""
+import numpy as np
+import pytest
+
+from paper_2602_14016_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.fail("a GPU test ran without a GPU")
+    from paper_2602_14016_gb300 import api as A, build
+
+    build.build()
+    return A
+
+
+def small(api, **kw):
+    base = dict(n=32, nsteps=8, dt=5e-3, nu=1e-3, px=8, every=4, kernels=[api.KernelSpec("exp_abs", 0.5)])
+    base.update(kw)
+    return api.Config(**base)
+
+
+def test_cost_grad_needs_observations(api):
+    from paper_2602_14016_gb300._native import DAError, DA_EINVAL
+
+    ctx = api.Context(small(api))
+    with pytest.raises(DAError) as e:
+        ctx.cost_grad(torch.zeros(1, 32, 32, dtype=torch.float64, device="cuda"))
+    assert e.value.status == DA_EINVAL
+
+
+def test_forward_only_context_rejects_adjoint(api):
+    from paper_2602_14016_gb300._native import DAError, DA_EINVAL
+
+    ctx = api.Context(small(api, store=False))
+    ctx.set_observations(torch.zeros(1, ctx.nt, 64, 2, dtype=torch.float64, device="cuda"))
+    with pytest.raises(DAError) as e:
+        ctx.cost_grad(torch.zeros(1, 32, 32, dtype=torch.float64, device="cuda"))
+    assert e.value.status == DA_EINVAL
+    wT, obs = ctx.forward(torch.zeros(1, 32, 32, dtype=torch.float64, device="cuda"))
+    assert torch.all(wT == 0) and torch.all(obs == 0)
+
+
+def test_launch_accounting_and_kernel_timing(api):
+    cfg = small(api)
+    ctx = api.Context(cfg)
+    s = ctx.control_from_omega(torch.from_numpy(synthetic.random_vorticity_hat(32, 1)[None]).cuda())
+    _, m = ctx.forward(s)
+    ctx.set_observations(m + 0.1)
+    l0 = ctx.launches
+    ctx.time_kernels("adj_rows")
+    J, g = ctx.cost_grad(s)
+    ms, cnt = ctx.kernel_time()
+    # forward: 2 + 8 per step + final observation; residual + init; adjoint 8 per step; gradient 2
+    assert ctx.launches - l0 == 2 + 8 * cfg.nsteps + 1 + 2 + 8 * cfg.nsteps + 2
+    assert cnt == 4 * cfg.nsteps and ms > 0
+    assert abs(J.item() - 0.5 * 0.01 * m.numel()) < 1e-9 * J.item()
+    ctx.time_kernels("off")
+
+
+def test_bitwise_deterministic(api):
+    ctx = api.Context(small(api, kernels=[api.KernelSpec("frac", 0.5), api.KernelSpec("identity", 0.0)]))
+    w = np.stack([synthetic.random_vorticity_hat(32, 3), synthetic.random_vorticity_hat(32, 4)])
+    s = ctx.control_from_omega(torch.from_numpy(w).cuda())
+    _, m = ctx.forward(s)
+    ctx.set_observations(m * 1.01)
+    J1, g1 = ctx.cost_grad(s * 0.9)
+    J2, g2 = ctx.cost_grad(s * 0.9)
+    assert torch.equal(J1, J2) and torch.equal(g1, g2)
