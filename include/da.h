@@ -166,6 +166,29 @@ da_status da_assimilate(da_ctx* ctx, double* s, int max_iter, const da_lbfgs_opt
 da_status da_omega_from_control(da_ctx* ctx, const double* s, double* omega0, void* stream);
 da_status da_control_from_omega(da_ctx* ctx, const double* omega0, double* s, void* stream);
 
+/* Control map s -> w0_hat of da_omega_from_control for ONE member, without
+ * a context and without allocating device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc, such as code inside a host framework that owns all device
+ * memory through its own pool, or a serving loop that must not allocate
+ * (or take the implicit synchronisation an allocation may bring) once it is
+ * running.  Its scratch is a file-scope static device array sized for
+ * n <= 256 (a 256 x 86 complex mixed field plus a 256-entry twiddle table,
+ * about 356 KB, held on every GPU that loads the library until exit).
+ *   n: 16, 32, 64, 128 or 256 (larger n: DA_EINVAL); nu: viscosity (used by
+ *   the heat kernel); kernel: identity, exp_abs, frac or exp_sq (a table
+ *   kernel: DA_EINVAL); s: DEVICE [n][n] double; omega0: DEVICE
+ *   [n][n/2+1] complex (every entry is written); message (nullable)
+ *   receives a static string describing a failure.
+ * The first call on a device sets that device up (it looks up the arrays'
+ * device addresses and copies the twiddles, synchronously); make that first
+ * call before any stream capture.  Every call shares the scratch: calls
+ * that can overlap on the GPU (other streams, other threads) race and must
+ * be serialised by the caller.  Each call writes every scratch entry it
+ * later reads, so no state carries over between calls. */
+da_status da_omega_from_control_static(int n, double nu, const da_kernel* kernel, const double* s, double* omega0,
+                                       void* stream, const char** message);
+
 /* Number of observation times of the context (nt). */
 int da_num_obs_times(const da_ctx* ctx);
 

@@ -22,8 +22,8 @@ KERNEL_KINDS = {"identity": 0, "exp_abs": 1, "frac": 2, "exp_sq": 3, "table": 4}
 # Entry points declared in include/da.h, in order.
 EXPORTS = ("da_create", "da_set_observations", "da_forward", "da_cost_grad", "da_last_adjoint",
            "da_adjoint_terminal", "da_assimilate", "da_omega_from_control", "da_control_from_omega",
-           "da_num_obs_times", "da_device_bytes", "da_launch_count", "da_time_kernels", "da_kernel_time",
-           "da_last_error", "da_destroy")
+           "da_omega_from_control_static", "da_num_obs_times", "da_device_bytes", "da_launch_count",
+           "da_time_kernels", "da_kernel_time", "da_last_error", "da_destroy")
 
 
 class Grid(ctypes.Structure):
@@ -82,6 +82,8 @@ def load(path: str = LIB_PATH):
             "da_assimilate": (I, [C, P, I, ctypes.POINTER(LbfgsOpts), P, P, P]),
             "da_omega_from_control": (I, [C, P, P, P]),
             "da_control_from_omega": (I, [C, P, P, P]),
+            "da_omega_from_control_static": (I, [I, D, ctypes.POINTER(Kernel), P, P, P,
+                                                 ctypes.POINTER(ctypes.c_char_p)]),
             "da_num_obs_times": (I, [C]),
             "da_device_bytes": (ctypes.c_ulonglong, [C]),
             "da_launch_count": (ctypes.c_ulonglong, [C]),
