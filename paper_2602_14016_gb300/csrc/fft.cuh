@@ -5,8 +5,9 @@
 // radix R and current sub-length L loads the R points x[i + m N/R] of
 // butterfly i, twiddles them by W_{LR}^{m (i mod L)}, applies an R-point DFT
 // in registers and stores them to y[(i - i mod L) R + i mod L + m L].  After
-// the last stage (L = N) the output is in natural order.  Stages ping-pong
-// between two buffers.  Twiddles come from a per-N table of
+// the last stage (L = N) the output is in natural order.  Stages work in
+// place: every thread holds its butterfly in registers across a barrier, so
+// one buffer of F sequences suffices.  Twiddles come from a per-N table of
 // W_N^t = exp(-2 pi i t / N) in shared memory; the inverse sign uses the
 // conjugate.  The R-point DFTs (R = 4, 8, 16) are written out by even/odd
 // splitting so that multiplications by +-i and +-1 cost nothing.
@@ -106,32 +107,59 @@ __device__ __forceinline__ void dftR(double2* a) {
   if constexpr (R == 16) dft16<S>(a);
 }
 
-// Radix plan per length: R1 x R2 (x R3).
-template <int N> struct Plan;
-template <> struct Plan<16> { static constexpr int R1 = 4, R2 = 4, R3 = 1; };
-template <> struct Plan<32> { static constexpr int R1 = 4, R2 = 8, R3 = 1; };
-template <> struct Plan<64> { static constexpr int R1 = 8, R2 = 8, R3 = 1; };
-template <> struct Plan<128> { static constexpr int R1 = 8, R2 = 16, R3 = 1; };
-template <> struct Plan<256> { static constexpr int R1 = 16, R2 = 16, R3 = 1; };
-template <> struct Plan<512> { static constexpr int R1 = 8, R2 = 8, R3 = 8; };
-template <> struct Plan<1024> { static constexpr int R1 = 16, R2 = 8, R3 = 8; };
+// Radix plans: a list of stage radices whose product is N.
+template <int... Rs>
+struct Radices {};
 
-// One Stockham stage on F sequences (leading dimension ld) by all CTA threads.
-template <int N, int R, int S>
-__device__ __forceinline__ void stockham_stage(const double2* __restrict__ src, double2* __restrict__ dst, int F,
-                                               int ld, int L, const double2* __restrict__ tw) {
+// Plan for four concurrent transforms (the widest radices keep the
+// instruction count lowest) and for a single transform (radices small enough
+// that every stage fills whole warps, so no lane idles in the FP64 pipe).
+template <int N> struct Plan;
+template <> struct Plan<16> { using four = Radices<4, 4>; using one = Radices<4, 4>; };
+template <> struct Plan<32> { using four = Radices<4, 8>; using one = Radices<4, 8>; };
+template <> struct Plan<64> { using four = Radices<8, 8>; using one = Radices<4, 4, 4>; };
+template <> struct Plan<128> { using four = Radices<8, 16>; using one = Radices<4, 4, 8>; };
+template <> struct Plan<256> { using four = Radices<16, 16>; using one = Radices<8, 8, 4>; };
+template <> struct Plan<512> { using four = Radices<8, 8, 8>; using one = Radices<8, 8, 8>; };
+template <> struct Plan<1024> { using four = Radices<16, 8, 8>; using one = Radices<16, 8, 8>; };
+
+template <typename P> struct MinRadix;
+template <int R> struct MinRadix<Radices<R>> { static constexpr int value = R; };
+template <int R, int... Rs> struct MinRadix<Radices<R, Rs...>> {
+  static constexpr int rest = MinRadix<Radices<Rs...>>::value;
+  static constexpr int value = R < rest ? R : rest;
+};
+
+template <int N>
+struct PlanInfo {
+  // threads that give every butterfly of four concurrent transforms (and of
+  // one transform) its own thread
+  static constexpr int T4 = 4 * N / MinRadix<typename Plan<N>::four>::value;
+  static constexpr int T1 = N / MinRadix<typename Plan<N>::one>::value;
+  static constexpr int TM = T4 > T1 ? T4 : T1;
+  static constexpr int THREADS = TM < 32 ? 32 : TM;
+};
+
+// One in-place Stockham stage on F sequences of N points stored back to back
+// in `buf`: every thread loads the R points of its butterfly, twiddles and
+// transforms them in registers, waits for all loads, then stores.
+template <int N, int R, int S, int F>
+__device__ __forceinline__ void stockham_stage(double2* buf, int L, const double2* __restrict__ tw) {
   constexpr int NB = N / R;
-  const int step = N / (L * R);
-  for (int u = threadIdx.x; u < F * NB; u += blockDim.x) {
+  static_assert(F * NB <= PlanInfo<N>::THREADS, "one butterfly per thread");
+  const int u = threadIdx.x;
+  const bool active = u < F * NB;
+  double2 a[R];
+  int base = 0, j = 0;
+  if (active) {
     const int f = u / NB;
     const int i = u - f * NB;
     const int k = i & (L - 1);
-    const double2* s = src + f * ld;
-    double2* d = dst + f * ld;
-    double2 a[R];
+    base = f * N;
 #pragma unroll
-    for (int m = 0; m < R; ++m) a[m] = s[i + m * NB];
+    for (int m = 0; m < R; ++m) a[m] = buf[base + i + m * NB];
     if (L > 1) {
+      const int step = N / (L * R);
 #pragma unroll
       for (int m = 1; m < R; ++m) {
         double2 w = tw[m * k * step];
@@ -140,30 +168,35 @@ __device__ __forceinline__ void stockham_stage(const double2* __restrict__ src, 
       }
     }
     dftR<R, S>(a);
-    const int j = (i - k) * R + k;
-#pragma unroll
-    for (int m = 0; m < R; ++m) d[j + m * L] = a[m];
+    j = (i - k) * R + k;
   }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) buf[base + j + m * L] = a[m];
+  }
+  __syncthreads();
 }
 
-// Transform F sequences in `a` (each N points, leading dimension ld); `b` is
-// scratch of the same shape.  Returns the buffer that holds the result.
-// Must be called by every thread of the CTA with `a` already synchronised;
-// returns after a final __syncthreads().
-template <int N, int S>
-__device__ __forceinline__ double2* fft_batch(double2* a, double2* b, int F, int ld, const double2* tw) {
-  using P = Plan<N>;
-  stockham_stage<N, P::R1, S>(a, b, F, ld, 1, tw);
-  __syncthreads();
-  stockham_stage<N, P::R2, S>(b, a, F, ld, P::R1, tw);
-  __syncthreads();
-  if constexpr (P::R3 > 1) {
-    stockham_stage<N, P::R3, S>(a, b, F, ld, P::R1 * P::R2, tw);
-    __syncthreads();
-    return b;
-  } else {
-    return a;
-  }
+template <int N, int S, int F, int L>
+__device__ __forceinline__ void run_stages(double2*, const double2*, Radices<>) {}
+
+template <int N, int S, int F, int L, int R, int... Rs>
+__device__ __forceinline__ void run_stages(double2* buf, const double2* tw, Radices<R, Rs...>) {
+  stockham_stage<N, R, S, F>(buf, L, tw);
+  run_stages<N, S, F, L * R>(buf, tw, Radices<Rs...>{});
+}
+
+// Transform, in place, F (1 or 4) sequences of N points stored back to back
+// in buf.  Called by every thread of a CTA of PlanInfo<N>::THREADS threads,
+// with buf already synchronised; returns after a final __syncthreads().
+template <int N, int S, int F>
+__device__ __forceinline__ void fft_batch(double2* buf, const double2* tw) {
+  static_assert(F == 1 || F == 4, "batches of one or four transforms");
+  if constexpr (F == 1)
+    run_stages<N, S, F, 1>(buf, tw, typename Plan<N>::one{});
+  else
+    run_stages<N, S, F, 1>(buf, tw, typename Plan<N>::four{});
 }
 
 }  // namespace da

@@ -66,13 +66,11 @@ struct Geo {
   static constexpr int Kc = K + 1;
   static constexpr int Kr = 2 * K + 1;
   static constexpr int NH = N / 2 + 1;
-  static constexpr int RMAX = Plan<N>::R1 > Plan<N>::R2 ? (Plan<N>::R1 > Plan<N>::R3 ? Plan<N>::R1 : Plan<N>::R3)
-                                                         : (Plan<N>::R2 > Plan<N>::R3 ? Plan<N>::R2 : Plan<N>::R3);
-  // threads: four transforms at a time, one butterfly of the widest stage each
-  static constexpr int THREADS = (4 * N / RMAX) < 32 ? 32 : 4 * N / RMAX;
-  // shared memory: twiddles + two buffers of four sequences + probe sums
+  // threads: four transforms at a time, one butterfly of each stage per thread
+  static constexpr int THREADS = PlanInfo<N>::THREADS;
+  // shared memory: twiddles + one buffer of four sequences + probe sums
   static constexpr int PMAX = 64;
-  static constexpr size_t SMEM = sizeof(double2) * (N + 8 * N + 2 * PMAX);
+  static constexpr size_t SMEM = sizeof(double2) * (N + 4 * N + 2 * PMAX);
 };
 
 __device__ __forceinline__ int ky_of_row(int r, int K) { return r <= K ? r : r - (2 * K + 1); }
@@ -128,17 +126,17 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_r2c_rows(Dev d, const double* __restrict__ in) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  double2 *tw = sm, *a = tw + N;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
   load_twiddles<N>(tw, d.tw);
   const double* r0 = in + ((size_t)bm * N + y0) * N;
   for (int x = threadIdx.x; x < N; x += blockDim.x) a[x] = make_double2(r0[x], r0[N + x]);
   __syncthreads();
-  const double2* Z = fft_batch<N, -1>(a, b, 1, N, tw);
+  fft_batch<N, -1, 1>(a, tw);
   double2* M = d.Mn + ((size_t)bm * N + y0) * G::Kc;
   for (int kx = threadIdx.x; kx < G::Kc; kx += blockDim.x) {
     double2 A, Bv;
-    unpack_pair<N>(Z, kx, A, Bv);
+    unpack_pair<N>(a, kx, A, Bv);
     M[kx] = A;
     M[G::Kc + kx] = Bv;
   }
@@ -150,17 +148,17 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_c2r_rows(Dev d, double* __restrict__ out) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  double2 *tw = sm, *a = tw + N;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
   load_twiddles<N>(tw, d.tw);
   const double2* M = d.Mn + ((size_t)bm * N + y0) * G::Kc;
   for (int kx = threadIdx.x; kx < N; kx += blockDim.x) a[kx] = pack_pair<N>(M, M + G::Kc, kx);
   __syncthreads();
-  const double2* z = fft_batch<N, +1>(a, b, 1, N, tw);
+  fft_batch<N, +1, 1>(a, tw);
   double* r0 = out + ((size_t)bm * N + y0) * N;
   for (int x = threadIdx.x; x < N; x += blockDim.x) {
-    r0[x] = z[x].x;
-    r0[N + x] = z[x].y;
+    r0[x] = a[x].x;
+    r0[N + x] = a[x].y;
   }
 }
 
@@ -170,27 +168,30 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_spec_to_mixed(Dev d, const double2* __restrict__ src, int mode) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  double2 *tw = sm, *a = tw + N;
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
-  for (int y = threadIdx.x; y < N; y += blockDim.x) a[y] = make_double2(0.0, 0.0);
-  __syncthreads();
   const double s = 1.0 / ((double)N * N);
-  for (int r = threadIdx.x; r < G::Kr; r += blockDim.x) {
-    const int ky = ky_of_row(r, G::K);
-    const size_t idx = ((size_t)bm * G::Kr + r) * G::Kc + kx;
-    const double m = d.mult[idx];
-    double f;
-    if (mode == M_ONE) f = 1.0;
-    else if (mode == M_CTRL) f = m;
-    else if (mode == M_FILTERED) f = (kx == 0 && ky == 0) ? 0.0 : m * m / sqrt((double)(kx * kx + ky * ky));
-    else f = m != 0.0 ? 1.0 / m : 0.0;
-    a[ky & (N - 1)] = cscale(src[idx], f * s);
+  for (int q = threadIdx.x; q < N; q += blockDim.x) {
+    const int ky = q < N / 2 ? q : q - N;
+    double2 v = make_double2(0.0, 0.0);
+    if (ky >= -G::K && ky <= G::K) {
+      const int r = ky >= 0 ? ky : ky + G::Kr;
+      const size_t idx = ((size_t)bm * G::Kr + r) * G::Kc + kx;
+      const double m = d.mult[idx];
+      double f;
+      if (mode == M_ONE) f = 1.0;
+      else if (mode == M_CTRL) f = m;
+      else if (mode == M_FILTERED) f = (kx == 0 && ky == 0) ? 0.0 : m * m / sqrt((double)(kx * kx + ky * ky));
+      else f = m != 0.0 ? 1.0 / m : 0.0;
+      v = cscale(src[idx], f * s);
+    }
+    a[q] = v;
   }
   __syncthreads();
-  const double2* z = fft_batch<N, +1>(a, b, 1, N, tw);
+  fft_batch<N, +1, 1>(a, tw);
   double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
-  for (int y = threadIdx.x; y < N; y += blockDim.x) M[(size_t)y * G::Kc] = z[y];
+  for (int y = threadIdx.x; y < N; y += blockDim.x) M[(size_t)y * G::Kc] = a[y];
 }
 
 // Compact <-> half-spectrum copies.  grid (ceil(N*NH/256), B), block 256.
@@ -225,8 +226,8 @@ __global__ void k_half_to_compact(const double2* __restrict__ in, double2* __res
 // Control map and the four inverse column transforms of a stage state
 // ---------------------------------------------------------------------------
 
-// Writes the four zero-padded columns (u, v, w_x, w_y of state value Yv at
-// compact row r, column kx, scaled by 1/N^2) into seq[0..3][N].
+// Writes the four column values (u, v, w_x, w_y of state value Yv at ky,
+// column kx, scaled by 1/N^2) into position q = ky mod N of seq[0..3][N].
 template <int N>
 __device__ __forceinline__ void put_stage_columns(double2* seq, int kx, int ky, double2 Yv) {
   const double k2 = (double)(kx * kx + ky * ky);
@@ -239,6 +240,16 @@ __device__ __forceinline__ void put_stage_columns(double2* seq, int kx, int ky, 
   seq[N + q] = make_double2(c * Ys.y, -c * Ys.x);              // v: -i kx / k^2
   seq[2 * N + q] = make_double2(-kx * Ys.y, kx * Ys.x);        // w_x: i kx
   seq[3 * N + q] = make_double2(-ky * Ys.y, ky * Ys.x);        // w_y: i ky
+}
+
+// Zeroes the positions outside the retained set in `nseq` sequences.
+template <int N>
+__device__ __forceinline__ void zero_outside(double2* seq, int nseq) {
+  constexpr int K = Geo<N>::K, GAP = N - 2 * K - 1;
+  for (int u = threadIdx.x; u < nseq * GAP; u += blockDim.x) {
+    const int f = u / GAP, q = K + 1 + (u - f * GAP);
+    seq[f * N + q] = make_double2(0.0, 0.0);
+  }
 }
 
 template <int N>
@@ -255,28 +266,27 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_ctrl_cols(Dev d, int flags) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  double2 *tw = sm, *a = tw + N;
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
   const double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
   for (int y = threadIdx.x; y < N; y += blockDim.x) a[y] = M[(size_t)y * G::Kc];
   __syncthreads();
-  double2* r = fft_batch<N, -1>(a, b, 1, N, tw);
-  double2* q = (r == a) ? b : a;
-  for (int u = threadIdx.x; u < 4 * N; u += blockDim.x) q[u] = make_double2(0.0, 0.0);
-  __syncthreads();
+  fft_batch<N, -1, 1>(a, tw);
+  // each retained position is read and rewritten by one thread only
   for (int rr = threadIdx.x; rr < G::Kr; rr += blockDim.x) {
     const int ky = ky_of_row(rr, G::K);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
-    const double2 w0 = cscale(r[ky & (N - 1)], d.mult[idx]);
+    const double2 w0 = cscale(a[ky & (N - 1)], d.mult[idx]);
     d.W[idx] = w0;
     d.Y[idx] = w0;
-    put_stage_columns<N>(q, kx, ky, w0);
+    put_stage_columns<N>(a, kx, ky, w0);
   }
   if (flags & F_NO_NEXT) return;
+  zero_outside<N>(a, 4);
   __syncthreads();
-  const double2* z = fft_batch<N, +1>(q, r, 4, N, tw);
-  store_mixed4<N>(d, z, bm, kx);
+  fft_batch<N, +1, 4>(a, tw);
+  store_mixed4<N>(d, a, bm, kx);
 }
 
 // ---------------------------------------------------------------------------
@@ -288,7 +298,7 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_rows(Dev d, int n, int stage, int flags) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  double2 *tw = sm, *a = tw + N;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
   load_twiddles<N>(tw, d.tw);
   const double2* M = d.Mx + (size_t)bm * 4 * N * G::Kc;
@@ -301,38 +311,43 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_rows(Dev d, int n, int 
     a[u] = pack_pair<N>(A, Bv, kx);
   }
   __syncthreads();
-  const double2* r = fft_batch<N, +1>(a, b, 4, N, tw);
-  double2* q = (r == a) ? b : a;
+  fft_batch<N, +1, 4>(a, tw);
   const int st = N / d.px;
   const int slot = (flags & (F_OBS | F_OBS_ONLY)) ? obs_slot(d, n) : -1;
   double* trj = (flags & F_STORE)
                     ? d.traj + (((size_t)bm * d.nsteps + n) * 4 + (stage - 1)) * 4 * (size_t)N * N
                     : nullptr;
-  for (int u = threadIdx.x; u < 2 * N; u += blockDim.x) {
-    const int rr = u / N, x = u - rr * N, y = y0 + rr;
-    const double2 uv = r[(2 * rr) * N + x], wg = r[(2 * rr + 1) * N + x];
-    if (trj) {
-      const size_t o = (size_t)y * N + x;
-      trj[o] = uv.x;
-      trj[(size_t)N * N + o] = uv.y;
-      trj[(size_t)2 * N * N + o] = wg.x;
-      trj[(size_t)3 * N * N + o] = wg.y;
+  // one thread per column x handles both rows, then overwrites a[x] only
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    double nl[2];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      const int y = y0 + rr;
+      const double2 uv = a[(2 * rr) * N + x], wg = a[(2 * rr + 1) * N + x];
+      if (trj) {
+        const size_t o = (size_t)y * N + x;
+        trj[o] = uv.x;
+        trj[(size_t)N * N + o] = uv.y;
+        trj[(size_t)2 * N * N + o] = wg.x;
+        trj[(size_t)3 * N * N + o] = wg.y;
+      }
+      if (slot >= 0 && (y % st) == 0 && (x % st) == 0) {
+        const int p = (y / st) * d.px + x / st;
+        double* o = d.obs + (((size_t)bm * d.nt + slot) * d.px * d.px + p) * 2;
+        o[0] = uv.x;
+        o[1] = uv.y;
+      }
+      nl[rr] = fma(uv.x, wg.x, uv.y * wg.y);
     }
-    if (slot >= 0 && (y % st) == 0 && (x % st) == 0) {
-      const int p = (y / st) * d.px + x / st;
-      double* o = d.obs + (((size_t)bm * d.nt + slot) * d.px * d.px + p) * 2;
-      o[0] = uv.x;
-      o[1] = uv.y;
-    }
-    reinterpret_cast<double*>(q)[2 * x + rr] = fma(uv.x, wg.x, uv.y * wg.y);
+    a[x] = make_double2(nl[0], nl[1]);
   }
   if (flags & F_OBS_ONLY) return;
   __syncthreads();
-  const double2* Z = fft_batch<N, -1>(q, const_cast<double2*>(r), 1, N, tw);
+  fft_batch<N, -1, 1>(a, tw);
   double2* O = d.Mn + ((size_t)bm * N + y0) * G::Kc;
   for (int kx = threadIdx.x; kx < G::Kc; kx += blockDim.x) {
     double2 A, Bv;
-    unpack_pair<N>(Z, kx, A, Bv);
+    unpack_pair<N>(a, kx, A, Bv);
     O[kx] = A;
     O[G::Kc + kx] = Bv;
   }
@@ -345,22 +360,20 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, int flags) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  double2 *tw = sm, *a = tw + N;
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
   const double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
   for (int y = threadIdx.x; y < N; y += blockDim.x) a[y] = M[(size_t)y * G::Kc];
   __syncthreads();
-  double2* r = fft_batch<N, -1>(a, b, 1, N, tw);
-  double2* q = (r == a) ? b : a;
-  for (int u = threadIdx.x; u < 4 * N; u += blockDim.x) q[u] = make_double2(0.0, 0.0);
-  __syncthreads();
+  fft_batch<N, -1, 1>(a, tw);
   const double dt = d.dt;
   const double fval = -d.amp * d.nf * (double)N * N / 2.0;
+  // each retained position is read and rewritten by one thread only
   for (int rr = threadIdx.x; rr < G::Kr; rr += blockDim.x) {
     const int ky = ky_of_row(rr, G::K);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
-    const double2 nh = r[ky & (N - 1)];
+    const double2 nh = a[ky & (N - 1)];
     const double2 yv = d.Y[idx];
     const double k2 = (double)(kx * kx + ky * ky);
     double2 F = make_double2(-nh.x - d.nu * k2 * yv.x, -nh.y - d.nu * k2 * yv.y);
@@ -385,12 +398,13 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, 
       d.W[idx] = ynext;
     }
     d.Y[idx] = ynext;
-    put_stage_columns<N>(q, kx, ky, ynext);
+    put_stage_columns<N>(a, kx, ky, ynext);
   }
   if (flags & F_NO_NEXT) return;
+  zero_outside<N>(a, 4);
   __syncthreads();
-  const double2* z = fft_batch<N, +1>(q, r, 4, N, tw);
-  store_mixed4<N>(d, z, bm, kx);
+  fft_batch<N, +1, 4>(a, tw);
+  store_mixed4<N>(d, a, bm, kx);
 }
 
 // r = model observations - data and J = 1/2 sum r^2 per member, in a fixed
@@ -445,12 +459,12 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_init(Dev d, int from_lambar) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *b = a + 4 * N, *Tu = b + 4 * N, *Tv = Tu + G::PMAX;
+  double2 *tw = sm, *a = tw + N, *Tu = a + 4 * N, *Tv = Tu + G::PMAX;
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
   const int slot = from_lambar ? -1 : obs_slot(d, d.nsteps);
   if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
-  for (int y = threadIdx.x; y < N; y += blockDim.x) a[y] = make_double2(0.0, 0.0);
+  zero_outside<N>(a, 1);
   __syncthreads();
   const double s = 1.0 / ((double)N * N);
   for (int rr = threadIdx.x; rr < G::Kr; rr += blockDim.x) {
@@ -464,9 +478,9 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_init(Dev d, int from_la
     a[ky & (N - 1)] = cscale(kb, s);
   }
   __syncthreads();
-  const double2* z = fft_batch<N, +1>(a, b, 1, N, tw);
+  fft_batch<N, +1, 1>(a, tw);
   double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
-  for (int y = threadIdx.x; y < N; y += blockDim.x) M[(size_t)y * G::Kc] = z[y];
+  for (int y = threadIdx.x; y < N; y += blockDim.x) M[(size_t)y * G::Kc] = a[y];
 }
 
 // Adjoint row pass of stage `stage` of step n: mu = inverse transform along x
@@ -476,32 +490,36 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_rows(Dev d, int n, int stage) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  double2 *tw = sm, *a = tw + N;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
   load_twiddles<N>(tw, d.tw);
   const double2* M = d.Mn + ((size_t)bm * N + y0) * G::Kc;
   for (int kx = threadIdx.x; kx < N; kx += blockDim.x) a[kx] = pack_pair<N>(M, M + G::Kc, kx);
   __syncthreads();
-  double2* r = fft_batch<N, +1>(a, b, 1, N, tw);
-  double2* q = (r == a) ? b : a;
+  fft_batch<N, +1, 1>(a, tw);
   const double* trj = d.traj + (((size_t)bm * d.nsteps + n) * 4 + (stage - 1)) * 4 * (size_t)N * N;
-  for (int u = threadIdx.x; u < 2 * N; u += blockDim.x) {
-    const int rr = u / N, x = u - rr * N;
-    const double mu = rr ? r[x].y : r[x].x;
-    const size_t o = (size_t)(y0 + rr) * N + x;
-    const double fu = trj[o], fv = trj[(size_t)N * N + o];
-    const double fwx = trj[(size_t)2 * N * N + o], fwy = trj[(size_t)3 * N * N + o];
-    q[(2 * rr) * N + x] = make_double2(fu * mu, fv * mu);
-    q[(2 * rr + 1) * N + x] = make_double2(fwx * mu, fwy * mu);
+  // one thread per column x reads a[x] (mu of both rows), then writes the
+  // four product sequences at x
+  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+    const double2 mu = a[x];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+      const double m = rr ? mu.y : mu.x;
+      const size_t o = (size_t)(y0 + rr) * N + x;
+      const double fu = trj[o], fv = trj[(size_t)N * N + o];
+      const double fwx = trj[(size_t)2 * N * N + o], fwy = trj[(size_t)3 * N * N + o];
+      a[(2 * rr) * N + x] = make_double2(fu * m, fv * m);
+      a[(2 * rr + 1) * N + x] = make_double2(fwx * m, fwy * m);
+    }
   }
   __syncthreads();
-  const double2* Z = fft_batch<N, -1>(q, r, 4, N, tw);
+  fft_batch<N, -1, 4>(a, tw);
   double2* O = d.Mx + (size_t)bm * 4 * N * G::Kc;
   for (int u = threadIdx.x; u < 4 * G::Kc; u += blockDim.x) {
     const int seq = u / G::Kc, kx = u - seq * G::Kc;
     const int rr = seq >> 1, g = seq & 1;
     double2 A, Bv;
-    unpack_pair<N>(Z + seq * N, kx, A, Bv);
+    unpack_pair<N>(a + seq * N, kx, A, Bv);
     O[((size_t)(2 * g) * N + y0 + rr) * G::Kc + kx] = A;
     O[((size_t)(2 * g + 1) * N + y0 + rr) * G::Kc + kx] = Bv;
   }
@@ -517,7 +535,7 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int stage, int flags) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *b = a + 4 * N, *Tu = b + 4 * N, *Tv = Tu + G::PMAX;
+  double2 *tw = sm, *a = tw + N, *Tu = a + 4 * N, *Tv = Tu + G::PMAX;
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
   const double2* M = d.Mx + (size_t)bm * 4 * N * G::Kc + kx;
@@ -525,17 +543,16 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int 
   const int slot = (flags & F_SRC) ? obs_slot(d, n) : -1;
   if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
   __syncthreads();
-  double2* r = fft_batch<N, -1>(a, b, 4, N, tw);
-  double2* q = (r == a) ? b : a;
-  for (int y = threadIdx.x; y < N; y += blockDim.x) q[y] = make_double2(0.0, 0.0);
-  __syncthreads();
+  fft_batch<N, -1, 4>(a, tw);
   const double dt = d.dt;
   const double s = 1.0 / ((double)N * N);
+  // each retained position is read (four sequences) and rewritten (first
+  // sequence) by one thread only
   for (int rr = threadIdx.x; rr < G::Kr; rr += blockDim.x) {
     const int ky = ky_of_row(rr, G::K);
     const int qi = ky & (N - 1);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
-    const double2 P1 = r[qi], P2 = r[N + qi], P3 = r[2 * N + qi], P4 = r[3 * N + qi];
+    const double2 P1 = a[qi], P2 = a[N + qi], P3 = a[2 * N + qi], P4 = a[3 * N + qi];
     const double k2 = (double)(kx * kx + ky * ky);
     const double ik2 = k2 > 0.0 ? 1.0 / k2 : 0.0;
     const double a1 = ky * ik2, c1 = kx * ik2;
@@ -569,13 +586,14 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int 
       nk = cscale(lam, dt / 6.0);
     }
     d.KB[idx] = nk;
-    q[qi] = cscale(nk, s);
+    a[qi] = cscale(nk, s);
   }
   if (flags & F_FINAL) return;
+  zero_outside<N>(a, 1);
   __syncthreads();
-  const double2* z = fft_batch<N, +1>(q, r, 1, N, tw);
+  fft_batch<N, +1, 1>(a, tw);
   double2* O = d.Mn + (size_t)bm * N * G::Kc + kx;
-  for (int y = threadIdx.x; y < N; y += blockDim.x) O[(size_t)y * G::Kc] = z[y];
+  for (int y = threadIdx.x; y < N; y += blockDim.x) O[(size_t)y * G::Kc] = a[y];
 }
 
 // Control multipliers m(k) = |k| W(k)^{1/2} on the retained set (0 at k = 0),

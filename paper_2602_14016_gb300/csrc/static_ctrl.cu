@@ -38,17 +38,17 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_rows(const double* __restri
                                                           const double2* __restrict__ tw256) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  double2 *tw = sm, *a = tw + N;
   const int y0 = 2 * blockIdx.x;
   load_tw<N>(tw, tw256);
   const double* r0 = s + (size_t)y0 * N;
   for (int x = threadIdx.x; x < N; x += blockDim.x) a[x] = make_double2(r0[x], r0[N + x]);
   __syncthreads();
-  const double2* Z = fft_batch<N, -1>(a, b, 1, N, tw);
+  fft_batch<N, -1, 1>(a, tw);
   double2* M = rows + (size_t)y0 * G::Kc;
   for (int kx = threadIdx.x; kx < G::Kc; kx += blockDim.x) {
     double2 A, Bv;
-    unpack_pair<N>(Z, kx, A, Bv);
+    unpack_pair<N>(a, kx, A, Bv);
     M[kx] = A;
     M[G::Kc + kx] = Bv;
   }
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_cols(const double2* __restr
                                                           double nu, double2* __restrict__ out) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *b = a + 4 * N;
+  double2 *tw = sm, *a = tw + N;
   const int kx = blockIdx.x;
   if (kx > G::K) {  // outside the retained set: zero column
     for (int q = threadIdx.x; q < N; q += blockDim.x) out[(size_t)q * G::NH + kx] = make_double2(0.0, 0.0);
@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_cols(const double2* __restr
   load_tw<N>(tw, tw256);
   for (int y = threadIdx.x; y < N; y += blockDim.x) a[y] = rows[(size_t)y * G::Kc + kx];
   __syncthreads();
-  const double2* r = fft_batch<N, -1>(a, b, 1, N, tw);
+  fft_batch<N, -1, 1>(a, tw);
+  const double2* r = a;
   for (int q = threadIdx.x; q < N; q += blockDim.x) {
     const int ky = q < N / 2 ? q : q - N;
     double2 v = make_double2(0.0, 0.0);
