@@ -62,8 +62,11 @@ typedef enum {
 /* Grid and time window.  n: points per side, a power of two in [16, 1024].
  * L: domain side, must be 2 pi (0 means 2 pi).  dt, nsteps: RK4 step and
  * count.  ckpt_every: 0 stores every stage field of every step for the
- * adjoint (the default; 128 n^2 bytes per step per member).  batch: members
- * per context (>= 1). */
+ * adjoint (the default; 128 n^2 bytes per step per member); K > 0 keeps the
+ * state every K steps and the stage fields of one K-step segment, and the
+ * adjoint recomputes each segment from its checkpoint (one extra forward
+ * solve; results are bitwise those of full storage); -1 keeps nothing
+ * (forward only).  batch: members per context (>= 1). */
 typedef struct {
   int n;
   double L;
@@ -137,6 +140,17 @@ da_status da_forward(da_ctx* ctx, const double* s, double* omegaT, double* obs, 
  * the call wait for the stream) and grad_s [batch][n][n] (device, may be
  * NULL).  Uses the observations of da_set_observations. */
 da_status da_cost_grad(da_ctx* ctx, const double* s, double* J, double* grad_s, void* stream);
+
+/* Vector-Jacobian product of the last da_forward on this context (which
+ * must have kept its trajectory, ckpt_every >= 0): the gradient with
+ * respect to the control s of <dobs, obs(s)> + <dwT, omega_T(s)>, i.e. the
+ * adjoint of Eq. (11) driven by arbitrary cotangents.  dobs: DEVICE
+ * [batch][nt][px*py][2] cotangent of the model observations (nullable);
+ * dwT: DEVICE [batch][n][n/2+1] complex, the DFT of the cotangent of the
+ * final vorticity grid values (nullable); grad_s: DEVICE [batch][n][n]
+ * (nullable).  da_cost_grad is the case dobs = obs - m, dwT = NULL.  With
+ * checkpoints, a second da_vjp needs a new da_forward. */
+da_status da_vjp(da_ctx* ctx, const double* dobs, const double* dwT, double* grad_s, void* stream);
 
 /* Optional extra outputs of the last da_cost_grad / da_adjoint_terminal on
  * this context: lam0 [batch][n][n/2+1] complex, the DFT of grad_{w0} J

@@ -37,7 +37,8 @@ class Config:
     every: int = 10
     include_t0: bool = False
     kernels: list = field(default_factory=lambda: [KernelSpec()])
-    store: bool = True  # keep stage fields for the adjoint (False: forward only)
+    store: bool = True  # keep the trajectory for the adjoint (False: forward only)
+    ckpt_every: int = 0  # 0: stage fields of every step; K > 0: checkpoint every K steps
 
     @property
     def batch(self) -> int:
@@ -69,7 +70,7 @@ class Context:
         self.lib = N.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
-        g = N.Grid(cfg.n, 0.0, cfg.dt, cfg.nsteps, 0 if cfg.store else -1, cfg.batch)
+        g = N.Grid(cfg.n, 0.0, cfg.dt, cfg.nsteps, cfg.ckpt_every if cfg.store else -1, cfg.batch)
         f = N.Forcing(1 if cfg.forcing == "kolmogorov" else 0, cfg.amp, cfg.nf)
         o = N.ObsOperator(cfg.px, cfg.px, cfg.every, int(cfg.include_t0))
         ks = (N.Kernel * cfg.batch)()
@@ -131,6 +132,17 @@ class Context:
         s = s_host.to(self.device, non_blocking=True)
         J, g = self.cost_grad(s, stream)
         return J.cpu(), g.cpu()
+
+    def vjp(self, dobs: torch.Tensor | None = None, dwT: torch.Tensor | None = None, stream=None):
+        """Gradient in s of <dobs, obs> + <dwT, omega_T> at the last forward."""
+        g = self._phys()
+        if dobs is not None:
+            dobs = dobs.to(self.device, torch.float64).contiguous()
+        dw = None
+        if dwT is not None:
+            dw = torch.view_as_real(dwT.to(self.device, torch.complex128).contiguous())
+        self._check(self.lib.da_vjp(self.ctx, _ptr(dobs), _ptr(dw), _ptr(g), _stream(stream)))
+        return g
 
     def last_adjoint(self, stream=None):
         """(lambda_0 half spectrum, G-metric gradient) of the last adjoint run."""

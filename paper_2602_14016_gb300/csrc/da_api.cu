@@ -33,6 +33,9 @@ struct da_ctx {
   unsigned long long launches = 0;
   bool have_obs = false;
   bool have_adj = false;
+  bool have_fwd = false;  // a stored forward (stage fields / checkpoints) is valid
+  int nckpt = 0;          // checkpoints held (ckpt > 0)
+  double2* ckpt_buf = nullptr;
   std::string err;
   // optimiser buffers (allocated on first da_assimilate)
   double *x = nullptr, *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr, *S = nullptr, *Y = nullptr;
@@ -141,7 +144,7 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
   if (!(grid->dt > 0.0) || !std::isfinite(grid->dt)) return fail(nullptr, DA_EINVAL, "dt must be positive");
   if (grid->nsteps < 1) return fail(nullptr, DA_EINVAL, "nsteps must be >= 1");
   if (grid->batch < 1) return fail(nullptr, DA_EINVAL, "batch must be >= 1");
-  if (grid->ckpt_every > 0) return fail(nullptr, DA_EINVAL, "checkpointing (ckpt_every > 0) is not available; use 0 (store all) or -1 (forward only)");
+  if (grid->ckpt_every < -1) return fail(nullptr, DA_EINVAL, "ckpt_every must be -1 (no store), 0 (all steps) or a checkpoint interval");
   if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(nullptr, DA_EINVAL, "nu must be >= 0");
   da_forcing f{DA_FORCE_NONE, 0.0, 0};
   if (forcing) f = *forcing;
@@ -205,7 +208,15 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
   A(dalloc(c, (double**)&d.mult, comp));
   A(dalloc(c, (double2**)&d.tw, N));
   A(dalloc(c, (double2**)&d.twP, (size_t)c->P));
-  if (c->ckpt == 0) A(dalloc(c, &d.traj, B * (size_t)c->nsteps * 16 * N * N));
+  // stage-field store: the whole window, or one checkpoint segment
+  if (c->ckpt == 0) {
+    d.traj_steps = c->nsteps;
+  } else if (c->ckpt > 0) {
+    d.traj_steps = std::min(c->ckpt, c->nsteps);
+    c->nckpt = (c->nsteps + c->ckpt - 1) / c->ckpt;
+    A(dalloc(c, &c->ckpt_buf, (size_t)c->nckpt * comp));
+  }
+  if (c->ckpt >= 0) A(dalloc(c, &d.traj, B * (size_t)d.traj_steps * 16 * N * N));
   int* d_kind = nullptr;
   double *d_param = nullptr, *d_table = nullptr;
   A(dalloc(c, &d_kind, B));
@@ -304,21 +315,34 @@ extern "C" da_status da_set_observations(da_ctx* c, const double* m, void* strea
   return DA_OK;
 }
 
-// Forward window from control s.  store: keep stage fields for the adjoint;
-// gather: fill the model observations.
-static da_status run_forward(da_ctx* c, const double* s, bool store, bool gather, cudaStream_t st) {
+// Forward window from control s.  With storage, the stage fields of every
+// step (ckpt == 0) or the state every ckpt steps plus the stage fields of the
+// last segment (ckpt > 0) are kept for the adjoint.  gather: fill the model
+// observations.
+static da_status run_forward(da_ctx* c, const double* s, bool gather, cudaStream_t st) {
   const Ops* o = c->ops;
-  const Dev& d = c->dev;
+  Dev& d = c->dev;
+  const bool store = d.traj != nullptr;
+  const int K = c->ckpt > 0 ? c->ckpt : c->nsteps;
+  const int last0 = ((c->nsteps - 1) / K) * K;  // first step of the last segment
+  const size_t comp = (size_t)c->B * o->Kr * o->Kc;
+  c->have_fwd = false;
   o->r2c_rows(d, s, st);
   o->ctrl_cols(d, 0, st);
   da_status r = check_launch(c, 2);
   if (r) return r;
+  d.seg0 = last0;
+  if (c->ckpt == 0) d.seg0 = 0;
   for (int k = 0; k < c->nsteps; ++k) {
+    if (c->ckpt > 0 && store && k % K == 0)
+      DA_TRY_CUDA(c, cudaMemcpyAsync(c->ckpt_buf + (size_t)(k / K) * comp, d.W, comp * sizeof(double2),
+                                     cudaMemcpyDeviceToDevice, st));
     const int obs_flag = (gather && obs_slot_host(c, k) >= 0) ? da::F_OBS : 0;
+    const int store_flag = (store && k >= d.seg0) ? da::F_STORE : 0;
     for (int j = 1; j <= 4; ++j) {
       {
         Timed t(c, 1, st);
-        o->fwd_rows(d, k, j, (store ? da::F_STORE : 0) | (j == 1 ? obs_flag : 0), st);
+        o->fwd_rows(d, k, j, store_flag | (j == 1 ? obs_flag : 0), st);
       }
       Timed t(c, 2, st);
       o->fwd_cols(d, j, 0, st);
@@ -329,28 +353,62 @@ static da_status run_forward(da_ctx* c, const double* s, bool store, bool gather
     o->fwd_rows(d, c->nsteps, 1, da::F_OBS_ONLY, st);
     if ((r = check_launch(c))) return r;
   }
+  c->have_fwd = store;
   return DA_OK;
 }
 
-// Backward sweep from the state in LamBar/KB/Mn (set by adj_init).
+// Backward sweep from the state in LamBar/KB/Mn (set by adj_init), segment by
+// segment from the last.  With checkpoints, every segment but the last is
+// first recomputed from its checkpoint (bitwise the same stage fields as the
+// first pass), then the inverse column transform of kbar, which the forward
+// recompute overwrote, is redone.
 static da_status run_adjoint(da_ctx* c, bool sources, cudaStream_t st) {
   const Ops* o = c->ops;
-  const Dev& d = c->dev;
+  Dev& d = c->dev;
+  const int K = c->ckpt > 0 ? c->ckpt : c->nsteps;
+  const int nseg = (c->nsteps + K - 1) / K;
+  const size_t comp = (size_t)c->B * o->Kr * o->Kc;
   da_status r;
-  for (int k = c->nsteps - 1; k >= 0; --k) {
-    for (int j = 4; j >= 1; --j) {
-      int flags = 0;
-      if (j == 1 && sources && obs_slot_host(c, k) >= 0) flags |= da::F_SRC;
-      if (j == 1 && k == 0) flags |= da::F_FINAL;
-      {
-        Timed t(c, 3, st);
-        o->adj_rows(d, k, j, st);
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int k0 = seg * K, k1 = std::min(k0 + K, c->nsteps);
+    if (seg != nseg - 1) {
+      DA_TRY_CUDA(c, cudaMemcpyAsync(d.W, c->ckpt_buf + (size_t)seg * comp, comp * sizeof(double2),
+                                     cudaMemcpyDeviceToDevice, st));
+      d.seg0 = k0;
+      o->state_cols(d, st);
+      if ((r = check_launch(c))) return r;
+      for (int k = k0; k < k1; ++k) {
+        for (int j = 1; j <= 4; ++j) {
+          {
+            Timed t(c, 1, st);
+            o->fwd_rows(d, k, j, da::F_STORE, st);
+          }
+          Timed t(c, 2, st);
+          o->fwd_cols(d, j, 0, st);
+        }
+        if ((r = check_launch(c, 8))) return r;
       }
-      Timed t(c, 4, st);
-      o->adj_cols(d, k, j, flags, st);
+      o->spec_to_mixed(d, d.KB, da::M_ONE, st);
+      if ((r = check_launch(c))) return r;
     }
-    if ((r = check_launch(c, 8))) return r;
+    d.seg0 = k0;
+    for (int k = k1 - 1; k >= k0; --k) {
+      for (int j = 4; j >= 1; --j) {
+        int flags = 0;
+        if (j == 1 && sources && obs_slot_host(c, k) >= 0) flags |= da::F_SRC;
+        if (j == 1 && k == 0) flags |= da::F_FINAL;
+        {
+          Timed t(c, 3, st);
+          o->adj_rows(d, k, j, st);
+        }
+        Timed t(c, 4, st);
+        o->adj_cols(d, k, j, flags, st);
+      }
+      if ((r = check_launch(c, 8))) return r;
+    }
   }
+  // the stored segment is now the first one; a later vjp must rerun the forward
+  c->have_fwd = c->ckpt == 0;
   return DA_OK;
 }
 
@@ -368,10 +426,17 @@ static da_status copy_scalars_out(da_ctx* c, double* J, cudaStream_t st) {
   return DA_OK;
 }
 
+static da_status gradient_out(da_ctx* c, double* grad_s, cudaStream_t st) {
+  if (!grad_s) return DA_OK;
+  c->ops->spec_to_mixed(c->dev, c->dev.LamBar, da::M_CTRL, st);
+  c->ops->c2r_rows(c->dev, grad_s, st);
+  return check_launch(c, 2);
+}
+
 extern "C" da_status da_forward(da_ctx* c, const double* s, double* omegaT, double* obs, void* stream) {
   if (!c || !s) return fail(c, DA_EINVAL, "ctx and s must not be NULL");
   cudaStream_t st = (cudaStream_t)stream;
-  da_status r = run_forward(c, s, false, obs != nullptr, st);
+  da_status r = run_forward(c, s, obs != nullptr, st);
   if (r) return r;
   if (omegaT) {
     c->ops->compact_to_half(c->dev, c->dev.W, (double2*)omegaT, st);
@@ -383,22 +448,15 @@ extern "C" da_status da_forward(da_ctx* c, const double* s, double* omegaT, doub
   return DA_OK;
 }
 
-static da_status gradient_out(da_ctx* c, double* grad_s, cudaStream_t st) {
-  if (!grad_s) return DA_OK;
-  c->ops->spec_to_mixed(c->dev, c->dev.LamBar, da::M_CTRL, st);
-  c->ops->c2r_rows(c->dev, grad_s, st);
-  return check_launch(c, 2);
-}
-
 extern "C" da_status da_cost_grad(da_ctx* c, const double* s, double* J, double* grad_s, void* stream) {
   if (!c || !s) return fail(c, DA_EINVAL, "ctx and s must not be NULL");
   if (!c->have_obs) return fail(c, DA_EINVAL, "no observations: call da_set_observations first");
   if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
   cudaStream_t st = (cudaStream_t)stream;
-  da_status r = run_forward(c, s, true, true, st);
+  da_status r = run_forward(c, s, true, st);
   if (r) return r;
   da::k_residual<<<c->B, 256, 0, st>>>(c->dev);
-  c->ops->adj_init(c->dev, 0, st);
+  c->ops->adj_init(c->dev, da::INIT_SRC, st);
   if ((r = check_launch(c, 2))) return r;
   if ((r = run_adjoint(c, true, st))) return r;
   c->have_adj = true;
@@ -410,12 +468,32 @@ extern "C" da_status da_adjoint_terminal(da_ctx* c, const double* s, const doubl
   if (!c || !s || !lamT) return fail(c, DA_EINVAL, "ctx, s and lamT must not be NULL");
   if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
   cudaStream_t st = (cudaStream_t)stream;
-  da_status r = run_forward(c, s, true, false, st);
+  da_status r = run_forward(c, s, false, st);
   if (r) return r;
   c->ops->half_to_compact(c->dev, (const double2*)lamT, c->dev.LamBar, st);
-  c->ops->adj_init(c->dev, 1, st);
+  c->ops->adj_init(c->dev, da::INIT_LAMBAR, st);
   if ((r = check_launch(c, 2))) return r;
   if ((r = run_adjoint(c, false, st))) return r;
+  c->have_adj = true;
+  return gradient_out(c, grad_s, st);
+}
+
+extern "C" da_status da_vjp(da_ctx* c, const double* dobs, const double* dwT, double* grad_s, void* stream) {
+  if (!c) return fail(c, DA_EINVAL, "ctx must not be NULL");
+  if (!c->have_fwd) return fail(c, DA_EINVAL, "da_vjp needs a stored forward: call da_forward on this context first");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nobs = (size_t)c->B * c->nt * c->P * c->P * 2;
+  if (dobs)
+    DA_TRY_CUDA(c, cudaMemcpyAsync(c->dev.res, dobs, nobs * sizeof(double), cudaMemcpyDefault, st));
+  if (dwT) {
+    c->ops->half_to_compact(c->dev, (const double2*)dwT, c->dev.LamBar, st);
+    da_status r = check_launch(c);
+    if (r) return r;
+  }
+  c->ops->adj_init(c->dev, (dwT ? da::INIT_LAMBAR : 0) | (dobs ? da::INIT_SRC : 0), st);
+  da_status r = check_launch(c);
+  if (r) return r;
+  if ((r = run_adjoint(c, dobs != nullptr, st))) return r;
   c->have_adj = true;
   return gradient_out(c, grad_s, st);
 }

@@ -52,26 +52,41 @@ __device__ __forceinline__ void dft2(double2* a) {
   a[1] = csub(t, a[1]);
 }
 
-// cos(pi/4), cos(pi/8), sin(pi/8)
+// cos(pi/4), cos(pi/8), tan(pi/8)
 constexpr double kR2 = 0.70710678118654752440;
 constexpr double kC8 = 0.92387953251128675613;
-constexpr double kS8 = 0.38268343236508977173;
+constexpr double kT8 = 0.41421356237309504880;
 
+// Output pair of a radix-2 combination with a scaled twiddle:
+// e +- c z, as two FMAs per component.
+__device__ __forceinline__ void bfly_scaled(const double2 e, const double2 z, double c, double2& plus, double2& minus) {
+  plus = make_double2(fma(c, z.x, e.x), fma(c, z.y, e.y));
+  minus = make_double2(fma(-c, z.x, e.x), fma(-c, z.y, e.y));
+}
+
+// Every twiddle w = exp(S i theta) of the internal combinations is written as
+// c (1 + i t) (or c (t + i)) with a constant tangent t, so that w o = c z
+// with z two FMAs (or two adds when t = 1), and e +- w o = e +- c z costs
+// four FMAs: six FP64 instructions instead of eight.
 template <int S>
 __device__ __forceinline__ void dft8(double2* a) {
   double2 e[4] = {a[0], a[2], a[4], a[6]};
   double2 o[4] = {a[1], a[3], a[5], a[7]};
   dft4<S>(e);
   dft4<S>(o);
-  // o_k *= exp(S i pi k / 4)
-  o[1] = make_double2((o[1].x - S * o[1].y) * kR2, (o[1].y + S * o[1].x) * kR2);
-  o[2] = mul_si<S>(o[2]);
-  o[3] = make_double2((-o[3].x - S * o[3].y) * kR2, (-o[3].y + S * o[3].x) * kR2);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    a[k] = cadd(e[k], o[k]);
-    a[k + 4] = csub(e[k], o[k]);
-  }
+  // k = 0
+  a[0] = cadd(e[0], o[0]);
+  a[4] = csub(e[0], o[0]);
+  // k = 2: w = S i
+  const double2 o2 = mul_si<S>(o[2]);
+  a[2] = cadd(e[2], o2);
+  a[6] = csub(e[2], o2);
+  // k = 1: w = (1 + S i)/sqrt2
+  const double2 z1 = make_double2(o[1].x - S * o[1].y, o[1].y + S * o[1].x);
+  bfly_scaled(e[1], z1, kR2, a[1], a[5]);
+  // k = 3: w = (-1 + S i)/sqrt2 = -(1 - S i)/sqrt2
+  const double2 z3 = make_double2(o[3].x + S * o[3].y, o[3].y - S * o[3].x);
+  bfly_scaled(e[3], z3, -kR2, a[3], a[7]);
 }
 
 template <int S>
@@ -84,19 +99,27 @@ __device__ __forceinline__ void dft16(double2* a) {
   }
   dft8<S>(e);
   dft8<S>(o);
-  // o_k *= exp(S i pi k / 8)
-  o[1] = cmul(o[1], make_double2(kC8, S * kS8));
-  o[2] = make_double2((o[2].x - S * o[2].y) * kR2, (o[2].y + S * o[2].x) * kR2);
-  o[3] = cmul(o[3], make_double2(kS8, S * kC8));
-  o[4] = mul_si<S>(o[4]);
-  o[5] = cmul(o[5], make_double2(-kS8, S * kC8));
-  o[6] = make_double2((-o[6].x - S * o[6].y) * kR2, (-o[6].y + S * o[6].x) * kR2);
-  o[7] = cmul(o[7], make_double2(-kC8, S * kS8));
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    a[k] = cadd(e[k], o[k]);
-    a[k + 8] = csub(e[k], o[k]);
-  }
+  // k = 0 and k = 4 (w = S i)
+  a[0] = cadd(e[0], o[0]);
+  a[8] = csub(e[0], o[0]);
+  const double2 o4 = mul_si<S>(o[4]);
+  a[4] = cadd(e[4], o4);
+  a[12] = csub(e[4], o4);
+  // k = 2, 6: w = (+-1 + S i)/sqrt2
+  const double2 z2 = make_double2(o[2].x - S * o[2].y, o[2].y + S * o[2].x);
+  bfly_scaled(e[2], z2, kR2, a[2], a[10]);
+  const double2 z6 = make_double2(o[6].x + S * o[6].y, o[6].y - S * o[6].x);
+  bfly_scaled(e[6], z6, -kR2, a[6], a[14]);
+  // k = 1, 3, 5, 7: w = cos(k pi/8) + S i sin(k pi/8) = c z with c = cos(pi/8)
+  // and z formed with t = tan(pi/8)
+  const double2 z1 = make_double2(fma(-S * kT8, o[1].y, o[1].x), fma(S * kT8, o[1].x, o[1].y));
+  bfly_scaled(e[1], z1, kC8, a[1], a[9]);
+  const double2 z3 = make_double2(fma(kT8, o[3].x, -S * o[3].y), fma(kT8, o[3].y, S * o[3].x));
+  bfly_scaled(e[3], z3, kC8, a[3], a[11]);
+  const double2 z5 = make_double2(fma(-kT8, o[5].x, -S * o[5].y), fma(-kT8, o[5].y, S * o[5].x));
+  bfly_scaled(e[5], z5, kC8, a[5], a[13]);
+  const double2 z7 = make_double2(fma(-S * kT8, o[7].y, -o[7].x), fma(S * kT8, o[7].x, -o[7].y));
+  bfly_scaled(e[7], z7, kC8, a[7], a[15]);
 }
 
 template <int R, int S>

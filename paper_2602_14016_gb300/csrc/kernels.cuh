@@ -37,6 +37,10 @@ enum : int {
   F_FINAL = 32     // adjoint column pass: last step (lambda_0 stays in LamBar)
 };
 
+// Start of the adjoint sweep (k_adj_init): add the observation source of
+// the last step, and/or start from the terminal field already in LamBar.
+enum : int { INIT_SRC = 1, INIT_LAMBAR = 2 };
+
 // Multipliers of the generic spectral-to-mixed column pass.
 enum : int { M_ONE = 0, M_CTRL = 1, M_FILTERED = 2, M_INV_CTRL = 3 };
 
@@ -50,7 +54,9 @@ struct Dev {
   double2 *W, *Acc, *Y, *KB, *LamBar, *Sum;  // compact [B][Kr][Kc]
   double2* Mx;                               // mixed [B][4][N][Kc]
   double2* Mn;                               // mixed [B][N][Kc]
-  double* traj;                              // [B][nsteps][4][4][N][N]
+  double* traj;                              // [B][traj_steps][4][4][N][N]
+  int traj_steps;                            // steps the stage-field store holds
+  int seg0;                                  // step stored in slot 0 of the store
   double* obs;                               // model observations [B][nt][P2][2]
   const double* mobs;                        // data [B][nt][P2][2]
   double* res;                               // residuals [B][nt][P2][2]
@@ -105,6 +111,32 @@ __device__ __forceinline__ double2 pack_pair(const double2* __restrict__ A, cons
   return make_double2(0.0, 0.0);
 }
 
+// Same packing for a whole sequence: every coefficient is loaded once and
+// written to kx and -kx; the gap K < kx < N-K is zeroed.  Loops run over
+// compile-time trip counts so that a thread's loads are issued together.
+template <int N, int T>
+__device__ __forceinline__ void pack_rows(double2* seq, const double2* __restrict__ A, const double2* __restrict__ Bv) {
+  constexpr int K = Geo<N>::K, GAP = N - 2 * K - 1;
+#pragma unroll
+  for (int t = 0; t < (GAP + T - 1) / T; ++t) {
+    const int u = threadIdx.x + t * T;
+    if (u < GAP) seq[K + 1 + u] = make_double2(0.0, 0.0);
+  }
+#pragma unroll
+  for (int t = 0; t < (K + 1 + T - 1) / T; ++t) {
+    const int kx = threadIdx.x + t * T;
+    if (kx <= K) {
+      const double2 p = A[kx], q = Bv[kx];
+      if (kx == 0) {
+        seq[0] = make_double2(p.x, q.x);
+      } else {
+        seq[kx] = make_double2(p.x - q.y, p.y + q.x);
+        seq[N - kx] = make_double2(p.x + q.y, q.x - p.y);
+      }
+    }
+  }
+}
+
 // The two half spectra packed in a forward transform Z of a + i b:
 // A(k) = (Z(k) + conj Z(-k))/2, B(k) = -i (Z(k) - conj Z(-k))/2.
 template <int N>
@@ -130,11 +162,13 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_r2c_rows(Dev d, const doubl
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
   load_twiddles<N>(tw, d.tw);
   const double* r0 = in + ((size_t)bm * N + y0) * N;
-  for (int x = threadIdx.x; x < N; x += blockDim.x) a[x] = make_double2(r0[x], r0[N + x]);
+  #pragma unroll
+  for (int x = threadIdx.x; x < N; x += G::THREADS) a[x] = make_double2(r0[x], r0[N + x]);
   __syncthreads();
   fft_batch<N, -1, 1>(a, tw);
   double2* M = d.Mn + ((size_t)bm * N + y0) * G::Kc;
-  for (int kx = threadIdx.x; kx < G::Kc; kx += blockDim.x) {
+  #pragma unroll
+  for (int kx = threadIdx.x; kx < G::Kc; kx += G::THREADS) {
     double2 A, Bv;
     unpack_pair<N>(a, kx, A, Bv);
     M[kx] = A;
@@ -152,11 +186,12 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_c2r_rows(Dev d, double* __r
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
   load_twiddles<N>(tw, d.tw);
   const double2* M = d.Mn + ((size_t)bm * N + y0) * G::Kc;
-  for (int kx = threadIdx.x; kx < N; kx += blockDim.x) a[kx] = pack_pair<N>(M, M + G::Kc, kx);
+  pack_rows<N, G::THREADS>(a, M, M + G::Kc);
   __syncthreads();
   fft_batch<N, +1, 1>(a, tw);
   double* r0 = out + ((size_t)bm * N + y0) * N;
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+  #pragma unroll
+  for (int x = threadIdx.x; x < N; x += G::THREADS) {
     r0[x] = a[x].x;
     r0[N + x] = a[x].y;
   }
@@ -172,7 +207,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_spec_to_mixed(Dev d, const 
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
   const double s = 1.0 / ((double)N * N);
-  for (int q = threadIdx.x; q < N; q += blockDim.x) {
+  #pragma unroll
+  for (int q = threadIdx.x; q < N; q += G::THREADS) {
     const int ky = q < N / 2 ? q : q - N;
     double2 v = make_double2(0.0, 0.0);
     if (ky >= -G::K && ky <= G::K) {
@@ -191,7 +227,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_spec_to_mixed(Dev d, const 
   __syncthreads();
   fft_batch<N, +1, 1>(a, tw);
   double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
-  for (int y = threadIdx.x; y < N; y += blockDim.x) M[(size_t)y * G::Kc] = a[y];
+  #pragma unroll
+  for (int y = threadIdx.x; y < N; y += G::THREADS) M[(size_t)y * G::Kc] = a[y];
 }
 
 // Compact <-> half-spectrum copies.  grid (ceil(N*NH/256), B), block 256.
@@ -256,7 +293,23 @@ template <int N>
 __device__ __forceinline__ void store_mixed4(const Dev& d, const double2* z, int bm, int kx) {
   using G = Geo<N>;
   double2* M = d.Mx + (size_t)bm * 4 * N * G::Kc + kx;
-  for (int u = threadIdx.x; u < 4 * N; u += blockDim.x) M[(size_t)u * G::Kc] = z[u];
+#pragma unroll
+  for (int t = 0; t < (4 * N + G::THREADS - 1) / G::THREADS; ++t) {
+    const int u = threadIdx.x + t * G::THREADS;
+    if (u < 4 * N) M[(size_t)u * G::Kc] = z[u];
+  }
+}
+
+// F whole columns (stride Kc, consecutive columns of F fields N*Kc apart)
+// into seq[f*N + y], with a compile-time trip count.
+template <int N, int T, int F>
+__device__ __forceinline__ void load_column(double2* seq, const double2* __restrict__ M) {
+  constexpr int Kc = Geo<N>::Kc;
+#pragma unroll
+  for (int t = 0; t < (F * N + T - 1) / T; ++t) {
+    const int u = threadIdx.x + t * T;
+    if (u < F * N) seq[u] = M[(size_t)u * Kc];
+  }
 }
 
 // s_hat = forward transform along y of the mixed rows in Mn; w0 = mult s_hat
@@ -270,11 +323,12 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_ctrl_cols(Dev d, int flags)
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
   const double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
-  for (int y = threadIdx.x; y < N; y += blockDim.x) a[y] = M[(size_t)y * G::Kc];
+  load_column<N, G::THREADS, 1>(a, M);
   __syncthreads();
   fft_batch<N, -1, 1>(a, tw);
   // each retained position is read and rewritten by one thread only
-  for (int rr = threadIdx.x; rr < G::Kr; rr += blockDim.x) {
+  #pragma unroll
+  for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
     const int ky = ky_of_row(rr, G::K);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
     const double2 w0 = cscale(a[ky & (N - 1)], d.mult[idx]);
@@ -284,6 +338,29 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_ctrl_cols(Dev d, int flags)
   }
   if (flags & F_NO_NEXT) return;
   zero_outside<N>(a, 4);
+  __syncthreads();
+  fft_batch<N, +1, 4>(a, tw);
+  store_mixed4<N>(d, a, bm, kx);
+}
+
+// Restart from the compact state in W (a checkpoint): Y = W and the four
+// inverse column transforms of stage 1.  grid (Kc, B).
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::THREADS) k_state_cols(Dev d) {
+  using G = Geo<N>;
+  extern __shared__ double2 sm[];
+  double2 *tw = sm, *a = tw + N;
+  const int kx = blockIdx.x, bm = blockIdx.y;
+  load_twiddles<N>(tw, d.tw);
+  zero_outside<N>(a, 4);
+  #pragma unroll
+  for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
+    const int ky = ky_of_row(rr, G::K);
+    const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+    const double2 w = d.W[idx];
+    d.Y[idx] = w;
+    put_stage_columns<N>(a, kx, ky, w);
+  }
   __syncthreads();
   fft_batch<N, +1, 4>(a, tw);
   store_mixed4<N>(d, a, bm, kx);
@@ -303,22 +380,22 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_rows(Dev d, int n, int 
   load_twiddles<N>(tw, d.tw);
   const double2* M = d.Mx + (size_t)bm * 4 * N * G::Kc;
   // sequence 2*rr + g packs row y0+rr of fields (2g, 2g+1): (u, v) or (w_x, w_y)
-  for (int u = threadIdx.x; u < 4 * N; u += blockDim.x) {
-    const int seq = u / N, kx = u - seq * N;
+#pragma unroll
+  for (int seq = 0; seq < 4; ++seq) {
     const int rr = seq >> 1, g = seq & 1;
-    const double2* A = M + ((size_t)(2 * g) * N + y0 + rr) * G::Kc;
-    const double2* Bv = M + ((size_t)(2 * g + 1) * N + y0 + rr) * G::Kc;
-    a[u] = pack_pair<N>(A, Bv, kx);
+    pack_rows<N, G::THREADS>(a + seq * N, M + ((size_t)(2 * g) * N + y0 + rr) * G::Kc,
+                             M + ((size_t)(2 * g + 1) * N + y0 + rr) * G::Kc);
   }
   __syncthreads();
   fft_batch<N, +1, 4>(a, tw);
   const int st = N / d.px;
   const int slot = (flags & (F_OBS | F_OBS_ONLY)) ? obs_slot(d, n) : -1;
   double* trj = (flags & F_STORE)
-                    ? d.traj + (((size_t)bm * d.nsteps + n) * 4 + (stage - 1)) * 4 * (size_t)N * N
+                    ? d.traj + (((size_t)bm * d.traj_steps + (n - d.seg0)) * 4 + (stage - 1)) * 4 * (size_t)N * N
                     : nullptr;
   // one thread per column x handles both rows, then overwrites a[x] only
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+  #pragma unroll
+  for (int x = threadIdx.x; x < N; x += G::THREADS) {
     double nl[2];
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
@@ -345,7 +422,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_rows(Dev d, int n, int 
   __syncthreads();
   fft_batch<N, -1, 1>(a, tw);
   double2* O = d.Mn + ((size_t)bm * N + y0) * G::Kc;
-  for (int kx = threadIdx.x; kx < G::Kc; kx += blockDim.x) {
+  #pragma unroll
+  for (int kx = threadIdx.x; kx < G::Kc; kx += G::THREADS) {
     double2 A, Bv;
     unpack_pair<N>(a, kx, A, Bv);
     O[kx] = A;
@@ -364,13 +442,14 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, 
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
   const double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
-  for (int y = threadIdx.x; y < N; y += blockDim.x) a[y] = M[(size_t)y * G::Kc];
+  load_column<N, G::THREADS, 1>(a, M);
   __syncthreads();
   fft_batch<N, -1, 1>(a, tw);
   const double dt = d.dt;
   const double fval = -d.amp * d.nf * (double)N * N / 2.0;
   // each retained position is read and rewritten by one thread only
-  for (int rr = threadIdx.x; rr < G::Kr; rr += blockDim.x) {
+  #pragma unroll
+  for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
     const int ky = ky_of_row(rr, G::K);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
     const double2 nh = a[ky & (N - 1)];
@@ -452,26 +531,27 @@ __device__ __forceinline__ double2 probe_source(const Dev& d, int kx, int ky, co
   return make_double2(a * Ru.y - c * Rv.y, -a * Ru.x + c * Rv.x);
 }
 
-// Start of the adjoint sweep: LamBar = H^T r at the last step (or, with
-// from_lambar, the terminal field already in LamBar), KB = dt/6 LamBar and
-// its inverse column transform into Mn.  grid (Kc, B).
+// Start of the adjoint sweep: LamBar = (terminal field in LamBar, with
+// INIT_LAMBAR) + (H^T r at the last step, with INIT_SRC), KB = dt/6 LamBar
+// and its inverse column transform into Mn.  grid (Kc, B).
 template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_init(Dev d, int from_lambar) {
+__global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_init(Dev d, int mode) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
   double2 *tw = sm, *a = tw + N, *Tu = a + 4 * N, *Tv = Tu + G::PMAX;
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
-  const int slot = from_lambar ? -1 : obs_slot(d, d.nsteps);
+  const int slot = (mode & INIT_SRC) ? obs_slot(d, d.nsteps) : -1;
   if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
   zero_outside<N>(a, 1);
   __syncthreads();
   const double s = 1.0 / ((double)N * N);
-  for (int rr = threadIdx.x; rr < G::Kr; rr += blockDim.x) {
+  #pragma unroll
+  for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
     const int ky = ky_of_row(rr, G::K);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
-    double2 lam = from_lambar ? d.LamBar[idx] : make_double2(0.0, 0.0);
-    if (slot >= 0) lam = probe_source(d, kx, ky, Tu, Tv);
+    double2 lam = (mode & INIT_LAMBAR) ? d.LamBar[idx] : make_double2(0.0, 0.0);
+    if (slot >= 0) lam = cadd(lam, probe_source(d, kx, ky, Tu, Tv));
     d.LamBar[idx] = lam;
     const double2 kb = cscale(lam, d.dt / 6.0);
     d.KB[idx] = kb;
@@ -480,7 +560,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_init(Dev d, int from_la
   __syncthreads();
   fft_batch<N, +1, 1>(a, tw);
   double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
-  for (int y = threadIdx.x; y < N; y += blockDim.x) M[(size_t)y * G::Kc] = a[y];
+  #pragma unroll
+  for (int y = threadIdx.x; y < N; y += G::THREADS) M[(size_t)y * G::Kc] = a[y];
 }
 
 // Adjoint row pass of stage `stage` of step n: mu = inverse transform along x
@@ -494,13 +575,14 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_rows(Dev d, int n, int 
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
   load_twiddles<N>(tw, d.tw);
   const double2* M = d.Mn + ((size_t)bm * N + y0) * G::Kc;
-  for (int kx = threadIdx.x; kx < N; kx += blockDim.x) a[kx] = pack_pair<N>(M, M + G::Kc, kx);
+  pack_rows<N, G::THREADS>(a, M, M + G::Kc);
   __syncthreads();
   fft_batch<N, +1, 1>(a, tw);
-  const double* trj = d.traj + (((size_t)bm * d.nsteps + n) * 4 + (stage - 1)) * 4 * (size_t)N * N;
+  const double* trj = d.traj + (((size_t)bm * d.traj_steps + (n - d.seg0)) * 4 + (stage - 1)) * 4 * (size_t)N * N;
   // one thread per column x reads a[x] (mu of both rows), then writes the
   // four product sequences at x
-  for (int x = threadIdx.x; x < N; x += blockDim.x) {
+  #pragma unroll
+  for (int x = threadIdx.x; x < N; x += G::THREADS) {
     const double2 mu = a[x];
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
@@ -515,7 +597,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_rows(Dev d, int n, int 
   __syncthreads();
   fft_batch<N, -1, 4>(a, tw);
   double2* O = d.Mx + (size_t)bm * 4 * N * G::Kc;
-  for (int u = threadIdx.x; u < 4 * G::Kc; u += blockDim.x) {
+  #pragma unroll
+  for (int u = threadIdx.x; u < 4 * G::Kc; u += G::THREADS) {
     const int seq = u / G::Kc, kx = u - seq * G::Kc;
     const int rr = seq >> 1, g = seq & 1;
     double2 A, Bv;
@@ -539,7 +622,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int 
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
   const double2* M = d.Mx + (size_t)bm * 4 * N * G::Kc + kx;
-  for (int u = threadIdx.x; u < 4 * N; u += blockDim.x) a[u] = M[(size_t)u * G::Kc];
+  load_column<N, G::THREADS, 4>(a, M);
   const int slot = (flags & F_SRC) ? obs_slot(d, n) : -1;
   if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
   __syncthreads();
@@ -548,7 +631,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int 
   const double s = 1.0 / ((double)N * N);
   // each retained position is read (four sequences) and rewritten (first
   // sequence) by one thread only
-  for (int rr = threadIdx.x; rr < G::Kr; rr += blockDim.x) {
+  #pragma unroll
+  for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
     const int ky = ky_of_row(rr, G::K);
     const int qi = ky & (N - 1);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
@@ -593,7 +677,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int 
   __syncthreads();
   fft_batch<N, +1, 1>(a, tw);
   double2* O = d.Mn + (size_t)bm * N * G::Kc + kx;
-  for (int y = threadIdx.x; y < N; y += blockDim.x) O[(size_t)y * G::Kc] = a[y];
+  #pragma unroll
+  for (int y = threadIdx.x; y < N; y += G::THREADS) O[(size_t)y * G::Kc] = a[y];
 }
 
 // Control multipliers m(k) = |k| W(k)^{1/2} on the retained set (0 at k = 0),

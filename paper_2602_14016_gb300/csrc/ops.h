@@ -18,7 +18,8 @@ struct Ops {
   void (*ctrl_cols)(const Dev&, int flags, cudaStream_t);
   void (*fwd_rows)(const Dev&, int n, int stage, int flags, cudaStream_t);
   void (*fwd_cols)(const Dev&, int stage, int flags, cudaStream_t);
-  void (*adj_init)(const Dev&, int from_lambar, cudaStream_t);
+  void (*state_cols)(const Dev&, cudaStream_t);
+  void (*adj_init)(const Dev&, int mode, cudaStream_t);
   void (*adj_rows)(const Dev&, int n, int stage, cudaStream_t);
   void (*adj_cols)(const Dev&, int n, int stage, int flags, cudaStream_t);
   void (*make_mult)(const Dev&, double* mult, const int* kind, const double* param, const double* table, double nu,

@@ -24,6 +24,7 @@ Ops make_ops() {
     set((const void*)k_ctrl_cols<N>);
     set((const void*)k_fwd_rows<N>);
     set((const void*)k_fwd_cols<N>);
+    set((const void*)k_state_cols<N>);
     set((const void*)k_adj_init<N>);
     set((const void*)k_adj_rows<N>);
     set((const void*)k_adj_cols<N>);
@@ -53,8 +54,11 @@ Ops make_ops() {
   o.fwd_cols = [](const Dev& d, int stage, int flags, cudaStream_t st) {
     k_fwd_cols<N><<<dim3(G::Kc, d.B), G::THREADS, G::SMEM, st>>>(d, stage, flags);
   };
-  o.adj_init = [](const Dev& d, int from_lambar, cudaStream_t st) {
-    k_adj_init<N><<<dim3(G::Kc, d.B), G::THREADS, G::SMEM, st>>>(d, from_lambar);
+  o.state_cols = [](const Dev& d, cudaStream_t st) {
+    k_state_cols<N><<<dim3(G::Kc, d.B), G::THREADS, G::SMEM, st>>>(d);
+  };
+  o.adj_init = [](const Dev& d, int mode, cudaStream_t st) {
+    k_adj_init<N><<<dim3(G::Kc, d.B), G::THREADS, G::SMEM, st>>>(d, mode);
   };
   o.adj_rows = [](const Dev& d, int n, int stage, cudaStream_t st) {
     k_adj_rows<N><<<dim3(N / 2, d.B), G::THREADS, G::SMEM, st>>>(d, n, stage);

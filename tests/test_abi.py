@@ -70,7 +70,7 @@ def _create(lib, n=64, nsteps=10, dt=1e-3, batch=1, px=8, every=5, nf=4, force=0
     (dict(force=1, nf=40), "forcing"),
     (dict(kind=9), "kernel"),
     (dict(kind=1, param=float("nan")), "finite"),
-    (dict(ckpt=4), "checkpoint"),
+    (dict(ckpt=-2), "ckpt_every"),
 ])
 def test_invalid_problems_are_rejected_on_the_host(lib, kw, frag):
     from paper_2602_14016_gb300 import _native as N
