@@ -35,13 +35,16 @@ _lib = None
 _lock = threading.Lock()
 
 KERNELS = {"identity": 0, "exp_abs": 1, "frac": 2, "exp_sq": 3, "table": 4}
+# no FMA contraction: the oracle rounds every operation as written, the same
+# way on x86 and Arm hosts
+_CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared"]
 
 
 def build(force: bool = False) -> str:
     """Compile da_oracle.c into libda_oracle.so next to it (gcc, -O2)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", *_CFLAGS, "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -61,6 +64,7 @@ class _Cfg(ctypes.Structure):
         ("kernel_kind", ctypes.c_int),
         ("kparam", ctypes.c_double),
         ("ktable", ctypes.c_void_p),
+        ("sobolev", ctypes.c_double),
     ]
 
 
@@ -81,6 +85,7 @@ class Problem:
     kernel: str = "identity"
     kparam: float = 0.0
     ktable: np.ndarray | None = None
+    sobolev: float = 0.0  # lambda of the regularisation term of Eq. (4)
 
     def cfg(self) -> _Cfg:
         c = _Cfg()
@@ -94,6 +99,7 @@ class Problem:
             c.ktable = self._tab.ctypes.data
         else:
             c.ktable = None
+        c.sobolev = self.sobolev
         return c
 
     @property
@@ -139,7 +145,7 @@ def compile_variant(source_text: str, out_path: str) -> str:
     src = out_path + ".c"
     with open(src, "w") as f:
         f.write(source_text)
-    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", out_path, src, "-lm"])
+    subprocess.check_call(["gcc", *_CFLAGS, "-o", out_path, src, "-lm"])
     return out_path
 
 
@@ -178,6 +184,8 @@ def _bind(lib):
         f.restype = None
     lib.orc_num_obs_times.argtypes = [C]
     lib.orc_num_obs_times.restype = ctypes.c_int
+    lib.orc_sobolev_term.argtypes = [C, P]
+    lib.orc_sobolev_term.restype = ctypes.c_double
     return lib
 
 
@@ -322,8 +330,17 @@ def adjoint_terminal(prob: Problem, s: np.ndarray, lamT: np.ndarray):
     return lam0, g
 
 
+def sobolev_term(prob: Problem, w0: np.ndarray) -> float:
+    """lambda/2 sum_grid |grad u0|^2 of Eq. (4) for the initial vorticity w0."""
+    c = prob.cfg()
+    return float(_load().orc_sobolev_term(ctypes.byref(c), _ptr(_spec(w0, prob.n))))
+
+
 def cost(prob: Problem, s: np.ndarray, m: np.ndarray) -> float:
     """J alone, from a forward solve (used by finite-difference pins)."""
     _, obs = forward(prob, s)
     r = obs - np.asarray(m).reshape(obs.shape)
-    return 0.5 * float(np.sum(r * r))
+    J = 0.5 * float(np.sum(r * r))
+    if prob.sobolev:
+        J += sobolev_term(prob, omega_from_control(prob, s))
+    return J

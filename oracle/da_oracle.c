@@ -50,6 +50,7 @@ typedef struct {
   int kernel_kind; /* 0 identity, 1 exp(-a|k|), 2 |k|^(-2a), 3 exp(-nu a k^2), 4 table */
   double kparam;   /* the kernel parameter a */
   const double* ktable; /* kind 4: W per half-spectrum mode, [n][n/2+1] */
+  double sobolev;  /* lambda of the regularisation term of Eq. (4); 0: none */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -571,6 +572,48 @@ void orc_forward(const orc_cfg* c, const double* s, double* wT, double* obs, dou
   free(w2);
 }
 
+/* Regularisation term of Eq. (4), lambda/2 sum over the grid of |grad u0|^2
+ * (sums over grid nodes replace the integral, as for every inner product
+ * here), with u0 the Biot-Savart velocity of w0: the four derivative fields
+ * du/dx, du/dy, dv/dx, dv/dy are formed spectrally and squared on the grid. */
+double orc_sobolev_term(const orc_cfg* c, const double* w0_in) {
+  int n = c->n, nn = n * nh(n);
+  const cplx* w0 = (const cplx*)w0_in;
+  cplx* t1 = xalloc(sizeof(cplx) * nn);
+  cplx* t2 = xalloc(sizeof(cplx) * nn);
+  double* f = xalloc(sizeof(double) * n * n);
+  symbol_fn vel[2] = {sym_u, sym_v}, der[2] = {sym_dx, sym_dy};
+  double sum = 0.0;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      apply_sym(w0, t1, n, vel[a], 0);
+      apply_sym(t1, t2, n, der[b], 0);
+      c2r(t2, f, n);
+      for (int i = 0; i < n * n; ++i) sum += f[i] * f[i];
+    }
+  free(t1); free(t2); free(f);
+  return 0.5 * c->sobolev * sum;
+}
+
+/* Gradient of the regularisation term with respect to the grid values of w0,
+ * as a DFT: lambda sum_{a,b} V_a^T D_b^T D_b V_a w0 (each factor transposed),
+ * accumulated into lam. */
+static void sobolev_gradient(const orc_cfg* c, const cplx* w0, cplx* lam) {
+  int n = c->n, nn = n * nh(n);
+  cplx* t1 = xalloc(sizeof(cplx) * nn);
+  cplx* t2 = xalloc(sizeof(cplx) * nn);
+  symbol_fn vel[2] = {sym_u, sym_v}, der[2] = {sym_dx, sym_dy};
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      apply_sym(w0, t1, n, vel[a], 0);
+      apply_sym(t1, t2, n, der[b], 0);
+      apply_sym(t2, t1, n, der[b], 1);
+      apply_sym(t1, t2, n, vel[a], 1);
+      for (int i = 0; i < nn; ++i) lam[i] += c->sobolev * t2[i];
+    }
+  free(t1); free(t2);
+}
+
 /* Cost J = 1/2 sum_j sum_i |u(x_i, t_j) - m_ij|^2 (Eq. 2-3) and its gradient
  * with respect to the control s.  The adjoint runs backward from
  * lambda_{nsteps} = H^T r_{nsteps} (terminal condition zero plus the source
@@ -587,6 +630,7 @@ void orc_cost_grad(const orc_cfg* c, const double* s, const double* m, double* J
     r[i] = obs[i] - m[i];
     Jv += 0.5 * r[i] * r[i];
   }
+  if (c->sobolev != 0.0) Jv += orc_sobolev_term(c, traj);
   *J = Jv;
   cplx* lam = xalloc(sizeof(cplx) * nn);
   cplx* lam2 = xalloc(sizeof(cplx) * nn);
@@ -602,6 +646,7 @@ void orc_cost_grad(const orc_cfg* c, const double* s, const double* m, double* J
       for (int i = 0; i < nn; ++i) lam[i] += src[i];
     }
   }
+  if (c->sobolev != 0.0) sobolev_gradient(c, (const cplx*)traj, lam);
   if (lam0) memcpy(lam0, lam, sizeof(cplx) * nn);
   if (g_s) orc_gradient_map(c, (double*)lam, g_s);
   free(traj); free(obs); free(r); free(lam); free(lam2); free(src);

@@ -182,3 +182,37 @@ def test_linear_limit_closed_form(orc):
     for j, step in enumerate([0, 3, 6]):
         expect += R**step * orc.observe_adj(P, r[j])
     assert rel(lam0, expect) < 1e-7
+
+
+def test_sobolev_term_single_mode(orc):
+    """Eq. (4) term for w0 = cos(ax + by): |grad u0|^2 = cos^2(ax + by), so
+    lambda/2 sum_grid |grad u0|^2 = lambda n^2 / 4."""
+    n = 16
+    y, x = np.meshgrid(2 * np.pi * np.arange(n) / n, 2 * np.pi * np.arange(n) / n, indexing="ij")
+    P = orc.Problem(n=n, nsteps=1, dt=1e-3, nu=0.0, px=4, every=1, sobolev=0.3)
+    w0 = np.fft.rfft2(np.cos(3 * x - 2 * y))
+    assert abs(orc.sobolev_term(P, w0) - 0.3 * n * n / 4) < 1e-12
+
+
+def test_sobolev_term_is_enstrophy_of_initial_field(orc):
+    """For a divergence-free periodic field sum |grad u|^2 = sum w^2 (grid sums)."""
+    n = 32
+    P = orc.Problem(n=n, nsteps=1, dt=1e-3, nu=0.0, px=4, every=1, sobolev=2.0)
+    w0 = synthetic.random_vorticity_hat(n, 3)
+    assert abs(orc.sobolev_term(P, w0) - np.sum(phys(w0) ** 2)) < 1e-12 * np.sum(phys(w0) ** 2)
+
+
+def test_regularised_gradient_against_central_differences(orc):
+    n = 16
+    P = orc.Problem(n=n, nsteps=6, dt=2e-2, nu=5e-3, px=4, every=2, kernel="exp_abs", kparam=0.3, sobolev=1e-2)
+    truth = orc.control_from_omega(P, synthetic.random_vorticity_hat(n, 20) * 2)
+    _, m = orc.forward(P, truth)
+    s = orc.control_from_omega(P, synthetic.random_vorticity_hat(n, 21) * 2)
+    J, g, _ = orc.cost_grad(P, s, m)
+    J0, g0, _ = orc.cost_grad(orc.Problem(**{**P.__dict__, "sobolev": 0.0}), s, m)
+    assert J > J0
+    for seed in range(3):
+        d = synthetic.random_field(n, 130 + seed)
+        eps = 1e-4
+        fd = (orc.cost(P, s + eps * d, m) - orc.cost(P, s - eps * d, m)) / (2 * eps)
+        assert abs(fd - np.sum(g * d)) < 1e-7 * abs(fd)

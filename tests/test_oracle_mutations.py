@@ -101,6 +101,16 @@ def battery(orc):
         a = dot(orc.omega_from_control(P, s), lam)
         return abs(a - float(np.sum(s * orc.gradient_map(P, lam)))) < 1e-12 * abs(a)
 
+    def sobolev_fd():
+        Q = orc.Problem(**{**P.__dict__, "sobolev": 1e-2})
+        truth = orc.control_from_omega(Q, synthetic.random_vorticity_hat(n, 20) * 2)
+        _, m = orc.forward(Q, truth)
+        s = orc.control_from_omega(Q, synthetic.random_vorticity_hat(n, 21) * 2)
+        _, g, _ = orc.cost_grad(Q, s, m)
+        d = synthetic.random_field(n, 31)
+        fd = (orc.cost(Q, s + 1e-4 * d, m) - orc.cost(Q, s - 1e-4 * d, m)) / 2e-4
+        return abs(fd - np.sum(g * d)) < 1e-7 * abs(fd)
+
     def gradient_fd():
         truth = orc.control_from_omega(P, synthetic.random_vorticity_hat(n, 20) * 2)
         _, m = orc.forward(P, truth)
@@ -114,7 +124,7 @@ def battery(orc):
                      ("kolmogorov", kolmogorov), ("conservation", conservation), ("rhs_dot", rhs_dot),
                      ("rhs_tangent", rhs_tangent), ("step", step_dot), ("obs_transpose", obs_transpose),
                      ("vorticity_control", vorticity_control), ("control_transpose", control_transpose),
-                     ("gradient_fd", gradient_fd)]:
+                     ("gradient_fd", gradient_fd), ("sobolev_fd", sobolev_fd)]:
         check(name, fn)
     return failed
 
@@ -136,6 +146,8 @@ MUTATIONS = [
      "o[i] = in_R(kx, ky, n) ? (acc[i] + c->nu * k2 * mu[i]) : 0;"),
     ("dealias_cut", "return abs(kx) <= K && abs(ky) <= K;", "return abs(kx) <= K + 1 && abs(ky) <= K + 1;"),
     ("nonlinear_term_dropped", "nl[i] = g.u[i] * g.wx[i] + g.v[i] * g.wy[i];", "nl[i] = g.u[i] * g.wx[i];"),
+    ("sobolev_gradient_sign", "for (int i = 0; i < nn; ++i) lam[i] += c->sobolev * t2[i];",
+     "for (int i = 0; i < nn; ++i) lam[i] -= c->sobolev * t2[i];"),
 ]
 
 
