@@ -127,6 +127,13 @@ typedef struct {
 da_status da_create(da_ctx** out, const da_grid* grid, double nu, const da_forcing* forcing,
                     const da_obs_operator* obs, const da_kernel* kernels);
 
+/* Sobolev regularisation of Eq. (4): da_cost_grad and da_assimilate add
+ * lambda/2 sum_grid |grad u0|^2 (= lambda/2 sum_grid w0^2 for the
+ * divergence-free initial field) to J and its gradient to grad_s.
+ * lambda >= 0; 0 (the default) turns it off.  Allocates one compact
+ * spectrum per member on the first non-zero lambda. */
+da_status da_set_sobolev(da_ctx* ctx, double lambda);
+
 /* Observations m, DEVICE pointer [batch][nt][px*py][2] with nt the number
  * of observation times; copied into the context on `stream`. */
 da_status da_set_observations(da_ctx* ctx, const double* m, void* stream);
@@ -164,6 +171,23 @@ da_status da_last_adjoint(da_ctx* ctx, double* lam0, double* filtered, void* str
  * DFT of a gradient with respect to the final vorticity; returns grad_s
  * [batch][n][n] (nullable).  Observations are not used. */
 da_status da_adjoint_terminal(da_ctx* ctx, const double* s, const double* lamT, double* grad_s, void* stream);
+
+/* Adjoint statistics of Sec. IV: the adjoint driven by the terminal field
+ * lamT (as da_adjoint_terminal) with, every save_every steps of backward
+ * time tau = (nsteps - k) dt (slot (nsteps - k)/save_every, from tau = 0 to
+ * the initial time), the energy per wavenumber shell k <= |k| < k+1 of the
+ * adjoint velocity u_dagger = (d lambda/dy, -d lambda/dx):
+ * E(k) = 1/2 sum over the shell of |u_dagger_hat|^2 with normalised Fourier
+ * coefficients (the shell sum of Eq. 20).  member: DEVICE
+ * [batch][nsteps/save_every + 1][nshell] per member (nullable); mean: DEVICE
+ * [nsteps/save_every + 1][nshell] of the ensemble-mean adjoint over the
+ * batch (nullable).  nshell = da_num_shells(ctx).  Reductions run in a fixed
+ * order.  save_every must divide nsteps. */
+da_status da_adjoint_spectra(da_ctx* ctx, const double* s, const double* lamT, int save_every, double* member,
+                             double* mean, void* stream);
+
+/* Number of wavenumber shells of da_adjoint_spectra: floor(sqrt(2) K) + 1. */
+int da_num_shells(const da_ctx* ctx);
 
 /* L-BFGS on s (in/out, [batch][n][n]) for up to max_iter iterations, each
  * member independently.  J_hist: HOST [batch][max_iter+1], the cost at the

@@ -106,6 +106,10 @@ class Context:
         N.check(st, self.ctx)
 
     # -- entry points ---------------------------------------------------------
+    def set_sobolev(self, lam: float):
+        """Regularisation lambda/2 sum |grad u0|^2 of Eq. (4) (0: off)."""
+        self._check(self.lib.da_set_sobolev(self.ctx, float(lam)))
+
     def set_observations(self, m: torch.Tensor, stream=None):
         m = m.to(self.device, torch.float64).contiguous()
         assert m.numel() == self.cfg.batch * self.nt * self.cfg.px ** 2 * 2
@@ -157,6 +161,18 @@ class Context:
         self._check(self.lib.da_adjoint_terminal(self.ctx, _ptr(s), _ptr(torch.view_as_real(lamT)), _ptr(g),
                                                  _stream(stream)))
         return g
+
+    def adjoint_spectra(self, s: torch.Tensor, lamT: torch.Tensor, save_every: int, stream=None):
+        """Shell energies of the adjoint velocity every save_every steps of
+        backward time: (per member [B, nsave, nshell], ensemble mean [nsave, nshell])."""
+        nshell = self.lib.da_num_shells(self.ctx)
+        nsave = self.cfg.nsteps // save_every + 1
+        member = torch.empty((self.cfg.batch, nsave, nshell), dtype=torch.float64, device=self.device)
+        mean = torch.empty((nsave, nshell), dtype=torch.float64, device=self.device)
+        lamT = torch.view_as_real(lamT.to(self.device, torch.complex128).contiguous())
+        self._check(self.lib.da_adjoint_spectra(self.ctx, _ptr(s.contiguous()), _ptr(lamT), save_every, _ptr(member),
+                                                _ptr(mean), _stream(stream)))
+        return member, mean
 
     def assimilate(self, s: torch.Tensor, max_iter: int, memory: int = 10, c1: float = 1e-4, c2: float = 0.9,
                    gtol_rel: float = 1e-10, max_ls_evals: int = 20, stream=None, raise_on_notconv: bool = False):

@@ -36,6 +36,12 @@ struct da_ctx {
   bool have_fwd = false;  // a stored forward (stage fields / checkpoints) is valid
   int nckpt = 0;          // checkpoints held (ckpt > 0)
   double2* ckpt_buf = nullptr;
+  double sobolev = 0.0;   // lambda of the regularisation term of Eq. (4)
+  // shell lists of the adjoint spectra (built on the first da_adjoint_spectra)
+  int nshell = 0;
+  int *shell_off = nullptr, *shell_mode = nullptr;
+  double *shell_wgt = nullptr, *shell_scratch = nullptr;
+  double2* w0 = nullptr;  // compact initial state kept for that term
   std::string err;
   // optimiser buffers (allocated on first da_assimilate)
   double *x = nullptr, *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr, *S = nullptr, *Y = nullptr;
@@ -307,6 +313,16 @@ extern "C" int da_num_obs_times(const da_ctx* c) { return c ? c->nt : 0; }
 extern "C" unsigned long long da_device_bytes(const da_ctx* c) { return c ? c->bytes : 0; }
 extern "C" unsigned long long da_launch_count(const da_ctx* c) { return c ? c->launches : 0; }
 
+extern "C" da_status da_set_sobolev(da_ctx* c, double lambda) {
+  if (!c || !std::isfinite(lambda) || lambda < 0.0) return fail(c, DA_EINVAL, "lambda must be finite and >= 0");
+  if (lambda != 0.0 && !c->w0) {
+    da_status r = dalloc(c, &c->w0, (size_t)c->B * c->ops->Kr * c->ops->Kc);
+    if (r) return r;
+  }
+  c->sobolev = lambda;
+  return DA_OK;
+}
+
 extern "C" da_status da_set_observations(da_ctx* c, const double* m, void* stream) {
   if (!c || !m) return fail(c, DA_EINVAL, "ctx and m must not be NULL");
   const size_t bytes = (size_t)c->B * c->nt * c->P * c->P * 2 * sizeof(double);
@@ -331,6 +347,7 @@ static da_status run_forward(da_ctx* c, const double* s, bool gather, cudaStream
   o->ctrl_cols(d, 0, st);
   da_status r = check_launch(c, 2);
   if (r) return r;
+  if (c->w0) DA_TRY_CUDA(c, cudaMemcpyAsync(c->w0, d.W, comp * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   d.seg0 = last0;
   if (c->ckpt == 0) d.seg0 = 0;
   for (int k = 0; k < c->nsteps; ++k) {
@@ -357,12 +374,45 @@ static da_status run_forward(da_ctx* c, const double* s, bool gather, cudaStream
   return DA_OK;
 }
 
+// Where the adjoint sweep records shell spectra (every `every` steps of
+// backward time, slot (nsteps - k)/every).
+struct SpectraOut {
+  int every = 0;
+  double* member = nullptr;  // [B][nsave][nshell]
+  double* mean = nullptr;    // [nsave][nshell]
+  double* scratch = nullptr; // [B][nshell]
+};
+
+static da_status record_spectra(da_ctx* c, const SpectraOut* sp, int k, cudaStream_t st) {
+  if (!sp || sp->every <= 0 || (c->nsteps - k) % sp->every) return DA_OK;
+  const int slot = (c->nsteps - k) / sp->every;
+  const int nsave = c->nsteps / sp->every + 1;
+  const int nmodes = c->ops->Kr * c->ops->Kc;
+  if (sp->member) {
+    da::k_shell_member<<<dim3(c->nshell, c->B), 128, 0, st>>>(c->dev.LamBar, c->shell_off, c->shell_mode,
+                                                              c->shell_wgt, nmodes, sp->scratch, c->nshell);
+    da_status r = check_launch(c);
+    if (r) return r;
+    // scratch [B][nshell] -> member[b][slot][:]
+    DA_TRY_CUDA(c, cudaMemcpy2DAsync(sp->member + (size_t)slot * c->nshell, (size_t)nsave * c->nshell * sizeof(double),
+                                     sp->scratch, (size_t)c->nshell * sizeof(double), c->nshell * sizeof(double), c->B,
+                                     cudaMemcpyDeviceToDevice, st));
+  }
+  if (sp->mean) {
+    da::k_shell_mean<<<c->nshell, 128, 0, st>>>(c->dev.LamBar, c->B, c->shell_off, c->shell_mode, c->shell_wgt,
+                                                 nmodes, sp->mean + (size_t)slot * c->nshell);
+    da_status r = check_launch(c);
+    if (r) return r;
+  }
+  return DA_OK;
+}
+
 // Backward sweep from the state in LamBar/KB/Mn (set by adj_init), segment by
 // segment from the last.  With checkpoints, every segment but the last is
 // first recomputed from its checkpoint (bitwise the same stage fields as the
 // first pass), then the inverse column transform of kbar, which the forward
 // recompute overwrote, is redone.
-static da_status run_adjoint(da_ctx* c, bool sources, cudaStream_t st) {
+static da_status run_adjoint(da_ctx* c, bool sources, cudaStream_t st, const SpectraOut* sp = nullptr) {
   const Ops* o = c->ops;
   Dev& d = c->dev;
   const int K = c->ckpt > 0 ? c->ckpt : c->nsteps;
@@ -405,6 +455,7 @@ static da_status run_adjoint(da_ctx* c, bool sources, cudaStream_t st) {
         o->adj_cols(d, k, j, flags, st);
       }
       if ((r = check_launch(c, 8))) return r;
+      if ((r = record_spectra(c, sp, k, st))) return r;
     }
   }
   // the stored segment is now the first one; a later vjp must rerun the forward
@@ -456,9 +507,18 @@ extern "C" da_status da_cost_grad(da_ctx* c, const double* s, double* J, double*
   da_status r = run_forward(c, s, true, st);
   if (r) return r;
   da::k_residual<<<c->B, 256, 0, st>>>(c->dev);
+  if (c->sobolev != 0.0) {
+    da::k_sobolev_cost<<<c->B, 256, 0, st>>>(c->dev.J, c->w0, c->sobolev, c->n, c->ops->Kr, c->ops->Kc);
+    if ((r = check_launch(c))) return r;
+  }
   c->ops->adj_init(c->dev, da::INIT_SRC, st);
   if ((r = check_launch(c, 2))) return r;
   if ((r = run_adjoint(c, true, st))) return r;
+  if (c->sobolev != 0.0) {
+    const int count = c->B * c->ops->Kr * c->ops->Kc;
+    da::k_sobolev_grad<<<(count + 255) / 256, 256, 0, st>>>(c->dev.LamBar, c->w0, c->sobolev, count);
+    if ((r = check_launch(c))) return r;
+  }
   c->have_adj = true;
   if ((r = gradient_out(c, grad_s, st))) return r;
   return copy_scalars_out(c, J, st);
@@ -496,6 +556,75 @@ extern "C" da_status da_vjp(da_ctx* c, const double* dobs, const double* dwT, do
   if ((r = run_adjoint(c, dobs != nullptr, st))) return r;
   c->have_adj = true;
   return gradient_out(c, grad_s, st);
+}
+
+// Mode lists per shell k <= |k| < k+1 over the compact set, with weights
+// (1 or 2) k^2 / (2 N^4) turning |lambda_hat|^2 into the shell energy of
+// the adjoint velocity.
+static da_status build_shells(da_ctx* c) {
+  if (c->nshell) return DA_OK;
+  const int K = c->ops->K, Kc = c->ops->Kc, Kr = c->ops->Kr;
+  const int nshell = (int)std::floor(std::sqrt(2.0) * K) + 1;
+  std::vector<std::vector<int>> modes(nshell);
+  std::vector<std::vector<double>> wgts(nshell);
+  const double n4 = std::pow((double)c->n, 4);
+  for (int r = 0; r < Kr; ++r)
+    for (int kx = 0; kx < Kc; ++kx) {
+      const int ky = r <= K ? r : r - Kr;
+      const double k2 = (double)kx * kx + (double)ky * ky;
+      if (k2 == 0.0) continue;
+      const int sh = (int)std::floor(std::sqrt(k2));
+      modes[sh].push_back(r * Kc + kx);
+      wgts[sh].push_back((kx == 0 ? 1.0 : 2.0) * k2 / (2.0 * n4));
+    }
+  std::vector<int> off(nshell + 1, 0), mode;
+  std::vector<double> wgt;
+  for (int sh = 0; sh < nshell; ++sh) {
+    off[sh + 1] = off[sh] + (int)modes[sh].size();
+    mode.insert(mode.end(), modes[sh].begin(), modes[sh].end());
+    wgt.insert(wgt.end(), wgts[sh].begin(), wgts[sh].end());
+  }
+  da_status r = DA_OK;
+  auto A = [&](da_status x) {
+    if (r == DA_OK) r = x;
+  };
+  A(dalloc(c, &c->shell_off, off.size()));
+  A(dalloc(c, &c->shell_mode, mode.size()));
+  A(dalloc(c, &c->shell_wgt, wgt.size()));
+  if (r) return r;
+  DA_TRY_CUDA(c, cudaMemcpy(c->shell_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+  DA_TRY_CUDA(c, cudaMemcpy(c->shell_mode, mode.data(), mode.size() * sizeof(int), cudaMemcpyHostToDevice));
+  DA_TRY_CUDA(c, cudaMemcpy(c->shell_wgt, wgt.data(), wgt.size() * sizeof(double), cudaMemcpyHostToDevice));
+  c->nshell = nshell;
+  return DA_OK;
+}
+
+extern "C" int da_num_shells(const da_ctx* c) { return c ? (int)std::floor(std::sqrt(2.0) * c->ops->K) + 1 : 0; }
+
+extern "C" da_status da_adjoint_spectra(da_ctx* c, const double* s, const double* lamT, int save_every,
+                                        double* member, double* mean, void* stream) {
+  if (!c || !s || !lamT) return fail(c, DA_EINVAL, "ctx, s and lamT must not be NULL");
+  if (save_every < 1 || c->nsteps % save_every) return fail(c, DA_EINVAL, "save_every must divide nsteps");
+  if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
+  da_status r = build_shells(c);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  SpectraOut sp;
+  sp.every = save_every;
+  sp.member = member;
+  sp.mean = mean;
+  if (member && !c->shell_scratch) {
+    if ((r = dalloc(c, &c->shell_scratch, (size_t)c->B * c->nshell))) return r;
+  }
+  sp.scratch = c->shell_scratch;
+  if ((r = run_forward(c, s, false, st))) return r;
+  c->ops->half_to_compact(c->dev, (const double2*)lamT, c->dev.LamBar, st);
+  c->ops->adj_init(c->dev, da::INIT_LAMBAR, st);
+  if ((r = check_launch(c, 2))) return r;
+  if ((r = record_spectra(c, &sp, c->nsteps, st))) return r;
+  if ((r = run_adjoint(c, false, st, &sp))) return r;
+  c->have_adj = true;
+  return DA_OK;
 }
 
 extern "C" da_status da_last_adjoint(da_ctx* c, double* lam0, double* filtered, void* stream) {

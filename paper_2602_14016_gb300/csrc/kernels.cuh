@@ -490,6 +490,21 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, 
 // order (deterministic).  grid B, block 256.  Defined in residual.cu.
 __global__ void k_residual(Dev d);
 
+// Regularisation of Eq. (4): J[b] += lambda/2 sum_grid w0^2, from the compact
+// initial spectrum w0 (sum_grid w^2 = 1/N^2 sum over the full spectrum).
+// grid B, block 256.  Defined in residual.cu.
+__global__ void k_sobolev_cost(double* J, const double2* w0, double lambda, int N, int Kr, int Kc);
+
+// Shell energies of the adjoint velocity, per member and of the ensemble
+// mean.  Defined in residual.cu.
+__global__ void k_shell_member(const double2* lam, const int* off, const int* mode, const double* wgt, int nmodes,
+                               double* out, int nshell);
+__global__ void k_shell_mean(const double2* lam, int B, const int* off, const int* mode, const double* wgt, int nmodes,
+                             double* out);
+
+// LamBar[b] += lambda w0[b] on the compact set.  Defined in residual.cu.
+__global__ void k_sobolev_grad(double2* lam, const double2* w0, double lambda, int count);
+
 // ---------------------------------------------------------------------------
 // Adjoint
 // ---------------------------------------------------------------------------

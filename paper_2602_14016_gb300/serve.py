@@ -1,0 +1,230 @@
+"""Serving assimilation jobs with continuous batching.
+
+Jobs (each a grid, window, probe set, kernel, observations, first guess and
+an L-BFGS iteration budget) arrive over time.  The server admits a job as
+soon as a worker slot is idle and the job's device memory fits the free
+budget; the job's trajectory storage is sized first (full stage fields, or
+checkpoints every K steps when the full window would exceed the per-job
+cap), so admission is by checkpoint memory.  Every slot runs its job on its
+own CUDA stream, so the kernels of concurrent jobs overlap on the device:
+a job that arrives while others run starts as soon as memory and a slot
+free up, without waiting for a batch boundary.  Each job's result does not
+depend on what else runs (own context, deterministic kernels).
+
+Reports per job: arrival, admission and completion times; overall:
+solves/s, p50/p99 latency.  `FakeExecutor` replaces the GPU for tests of
+the admission and accounting logic on the CPU.
+"""
+from __future__ import annotations
+
+import dataclasses
+import heapq
+import threading
+import time
+from typing import Callable, Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Job:
+    job_id: int
+    n: int
+    nsteps: int
+    dt: float
+    nu: float
+    px: int
+    every: int
+    kernel: tuple = ("identity", 0.0)
+    forcing: str = "none"
+    nf: int = 4
+    iters: int = 30
+    arrival: float = 0.0  # seconds after the start of the run
+    m: Optional[np.ndarray] = None  # observations [1, nt, px*px, 2]
+    s0: Optional[np.ndarray] = None  # first guess [1, n, n]
+    # filled by the server
+    ckpt_every: int = 0
+    bytes: int = 0
+    t_admit: float = float("nan")
+    t_done: float = float("nan")
+    J_hist: Optional[np.ndarray] = None
+    iters_done: int = 0
+    status: int = -1
+    s: Optional[np.ndarray] = None
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.arrival
+
+    @property
+    def nt(self) -> int:
+        return self.nsteps // self.every
+
+
+def context_bytes(n: int, nsteps: int, px: int, every: int, ckpt_every: int, batch: int = 1, memory: int = 10) -> int:
+    """Device bytes of a context plus its optimiser buffers (mirrors da_create
+    and da_assimilate's allocations)."""
+    K = (n - 1) // 3
+    Kc, Kr = K + 1, 2 * K + 1
+    nt = nsteps // every
+    comp = batch * Kr * Kc * 16
+    b = 6 * comp + batch * 5 * n * Kc * 16 + 3 * batch * nt * px * px * 2 * 8 + comp // 2
+    b += n * 16 + px * 16 + batch * (8 + 4 + 8) + batch * 8
+    if ckpt_every == 0:
+        b += batch * nsteps * 16 * n * n * 8
+    else:
+        kk = min(ckpt_every, nsteps)
+        b += batch * kk * 16 * n * n * 8 + ((nsteps + kk - 1) // kk) * comp
+    slots = memory + 1
+    b += batch * (5 + 2 * slots) * n * n * 8 + batch * (((n * n + 8191) // 8192) + 3) * 8 + 2 * batch * 8
+    return int(b)
+
+
+def plan_storage(job: Job, job_cap_bytes: int) -> None:
+    """Full stage-field storage if it fits the per-job cap, else the largest
+    checkpoint interval (a divisor-free K, last segment shorter) that fits."""
+    full = context_bytes(job.n, job.nsteps, job.px, job.every, 0)
+    if full <= job_cap_bytes:
+        job.ckpt_every, job.bytes = 0, full
+        return
+    for K in range(job.nsteps, 0, -1):
+        b = context_bytes(job.n, job.nsteps, job.px, job.every, K)
+        if b <= job_cap_bytes:
+            job.ckpt_every, job.bytes = K, b
+            return
+    job.ckpt_every, job.bytes = 1, context_bytes(job.n, job.nsteps, job.px, job.every, 1)
+
+
+class CudaExecutor:
+    """Runs a job through the C ABI on the slot's stream."""
+
+    def __init__(self, device: int = 0):
+        import torch
+
+        self.torch = torch
+        self.device = device
+        self.streams = {}
+
+    def run(self, job: Job, slot: int) -> None:
+        torch = self.torch
+        from . import api
+
+        if slot not in self.streams:
+            with torch.cuda.device(self.device):
+                self.streams[slot] = torch.cuda.Stream()
+        st = self.streams[slot]
+        cfg = api.Config(n=job.n, nsteps=job.nsteps, dt=job.dt, nu=job.nu, forcing=job.forcing, nf=job.nf,
+                         px=job.px, every=job.every, kernels=[api.KernelSpec(*job.kernel)],
+                         ckpt_every=job.ckpt_every)
+        with torch.cuda.device(self.device), torch.cuda.stream(st):
+            ctx = api.Context(cfg, self.device)
+            try:
+                ctx.set_observations(torch.from_numpy(job.m).to(ctx.device), stream=st)
+                s = torch.from_numpy(job.s0).to(ctx.device).contiguous()
+                J, it, status = ctx.assimilate(s, job.iters, stream=st)
+                st.synchronize()
+                job.J_hist, job.iters_done, job.status = J[0], int(it[0]), int(status)
+                job.s = s.cpu().numpy()
+            finally:
+                ctx.close()
+
+
+class FakeExecutor:
+    """Stands in for the GPU: a job takes `seconds(job)` of wall time."""
+
+    def __init__(self, seconds: Callable[[Job], float]):
+        self.seconds = seconds
+
+    def run(self, job: Job, slot: int) -> None:
+        time.sleep(self.seconds(job))
+        job.status, job.iters_done = 0, job.iters
+        job.J_hist = np.zeros(job.iters + 1)
+
+
+class Server:
+    """Admission by memory, one job per slot at a time, slots run concurrently."""
+
+    def __init__(self, executor, memory_budget: int, slots: int = 4, job_cap: Optional[int] = None):
+        self.executor = executor
+        self.budget = int(memory_budget)
+        self.slots = slots
+        self.job_cap = int(job_cap) if job_cap else int(memory_budget)
+        self._lock = threading.Condition()
+        self._free_bytes = self.budget
+        self._idle = list(range(slots))
+        self._queue: list = []
+        self._running = 0
+        self.peak_bytes = 0
+        self.peak_running = 0
+
+    def _admit_locked(self, now: float, t0: float):
+        """First-fit over the queue in arrival order."""
+        started = []
+        i = 0
+        while i < len(self._queue) and self._idle:
+            job = self._queue[i]
+            if job.bytes <= self._free_bytes:
+                self._queue.pop(i)
+                slot = self._idle.pop(0)
+                self._free_bytes -= job.bytes
+                self._running += 1
+                self.peak_bytes = max(self.peak_bytes, self.budget - self._free_bytes)
+                self.peak_running = max(self.peak_running, self._running)
+                job.t_admit = now - t0
+                started.append((job, slot))
+            else:
+                i += 1
+        return started
+
+    def run(self, jobs: list) -> dict:
+        """Replays the jobs' arrival times; returns the summary."""
+        for j in jobs:
+            plan_storage(j, self.job_cap)
+            if j.bytes > self.budget:
+                raise ValueError(f"job {j.job_id} needs {j.bytes} bytes, more than the budget")
+        pending = sorted(jobs, key=lambda j: j.arrival)
+        t0 = time.perf_counter()
+        threads = []
+
+        def work(job, slot):
+            try:
+                self.executor.run(job, slot)
+            finally:
+                with self._lock:
+                    job.t_done = time.perf_counter() - t0
+                    self._free_bytes += job.bytes
+                    self._idle.append(slot)
+                    self._idle.sort()
+                    self._running -= 1
+                    self._lock.notify_all()
+
+        k = 0
+        while k < len(pending) or self._queue or self._running:
+            with self._lock:
+                now = time.perf_counter()
+                while k < len(pending) and pending[k].arrival <= now - t0:
+                    self._queue.append(pending[k])
+                    k += 1
+                for job, slot in self._admit_locked(now, t0):
+                    th = threading.Thread(target=work, args=(job, slot), daemon=True)
+                    th.start()
+                    threads.append(th)
+                if k >= len(pending) and not self._queue and not self._running:
+                    break
+                wait = None
+                if k < len(pending):
+                    wait = max(0.0, pending[k].arrival - (time.perf_counter() - t0))
+                self._lock.wait(timeout=wait if wait is not None else 0.5)
+        for th in threads:
+            th.join()
+        makespan = max(j.t_done for j in jobs) - min(j.arrival for j in jobs)
+        lat = np.array([j.latency for j in jobs])
+        return {"jobs": len(jobs), "solves_per_s": len(jobs) / makespan, "makespan_s": makespan,
+                "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                "peak_bytes": self.peak_bytes, "peak_running": self.peak_running}
+
+
+def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
+    """Arrival times of a Poisson process (seeded exponential gaps)."""
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=count)
+    return np.cumsum(gaps) - gaps[0]

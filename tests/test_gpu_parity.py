@@ -212,3 +212,21 @@ def test_gradient_against_gpu_finite_differences(api):
     Jm, _ = ctx.cost_grad(s - eps * d)
     fd = (Jp.item() - Jm.item()) / (2 * eps)
     assert abs(fd - gd) < 1e-6 * abs(gd)
+
+
+@pytest.mark.parametrize("ckpt", [0, 3])
+def test_sobolev_regularised_cost_and_gradient(orc, api, ckpt):
+    n = 32
+    probs, cfg = make_pair(orc, n, 12, 5e-3, 1e-3, kernels=[("exp_abs", 0.5)], px=8, every=4)
+    cfg.ckpt_every = ckpt
+    P = probs[0]
+    P.sobolev = 1e-2
+    truth, guess = truth_and_guess(orc, P, 150, 151, scale=2.0)
+    _, m = orc.forward(P, truth)
+    J, g, _ = orc.cost_grad(P, guess, m)
+    ctx = api.Context(cfg)
+    ctx.set_sobolev(1e-2)
+    ctx.set_observations(cu(m[None]))
+    Jg, gg = ctx.cost_grad(cu(guess[None]))
+    assert abs(Jg.item() - J) <= COST_TOL * J
+    assert rel(gg.cpu().numpy()[0], g) < GRAD_TOL
