@@ -138,36 +138,6 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def first_guess_from_probes(w_hat: np.ndarray, n: int, px: int) -> np.ndarray:
-    """Vorticity of the trigonometric interpolation of the t = 0 probe velocities.
-
-    Input preparation on the host (numpy): u, v of the truth at the probe
-    lattice, their px x px DFT, vorticity i kx v - i ky u on the coarse
-    modes, zero-padded into the n^2 half spectrum."""
-    from paper_2602_14016_gb300 import synthetic
-
-    KX, KY = synthetic.wavenumbers(n)
-    k2 = (KX**2 + KY**2).astype(float)
-    ik2 = np.where(k2 > 0, 1.0 / np.where(k2 > 0, k2, 1.0), 0.0)
-    u = np.fft.irfft2(1j * KY * ik2 * w_hat, s=(n, n))
-    v = np.fft.irfft2(-1j * KX * ik2 * w_hat, s=(n, n))
-    st = n // px
-    uc, vc = u[::st, ::st], v[::st, ::st]
-    Uc, Vc = np.fft.rfft2(uc), np.fft.rfft2(vc)
-    kxc, kyc = np.meshgrid(np.arange(px // 2 + 1), np.fft.fftfreq(px, 1.0 / px).astype(int))
-    Wc = 1j * kxc * Vc - 1j * kyc * Uc
-    out = np.zeros((n, n // 2 + 1), complex)
-    scale = (n / px) ** 2
-    for q in range(px):
-        ky = kyc[q, 0]
-        if abs(ky) >= px // 2:
-            continue
-        for p in range(px // 2):
-            out[ky % n, p] = Wc[q, p] * scale
-    out[0, 0] = 0
-    return out
-
-
 def prepare(api, torch, kernels, device):
     """Spin-up, truth observations with noise, first-guess controls."""
     from paper_2602_14016_gb300 import synthetic
@@ -192,6 +162,8 @@ def prepare(api, torch, kernels, device):
     w_truth = w.cpu().numpy()[0]
     spin.close()
     win.close()
+    from paper_2602_14016_gb300.workloads import first_guess_from_probes
+
     w_guess = first_guess_from_probes(w_truth, n, W["px"])
     B = len(kernels)
     return np.repeat(m[None], B, 0), np.repeat(w_guess[None], B, 0), w_truth
@@ -225,29 +197,30 @@ def run_gpu(args):
     s = ctx.control_from_omega(torch.from_numpy(w_guess).to(device))
     stream = torch.cuda.current_stream()
 
-    # warm-up; with at least four, the first four also time one pass-kernel
-    # class each and the dominant class is the one timed below
+    # warm-up; with at least four, the first four time one pass-kernel class
+    # each (direct launches), the rest replay the captured CUDA graph
     classes = ["fwd_rows", "fwd_cols", "adj_rows", "adj_cols"]
     class_ms = {}
-    J = None
-    for i in range(args.warmup):
+    warm = max(args.warmup, 5 if args.warmup >= 4 else 1) if args.graphs else args.warmup
+    for i in range(warm):
         timed = i < 4 and args.warmup >= 4
         if timed:
             ctx.time_kernels(classes[i])
+        else:
+            ctx.time_kernels("off")
+            ctx.set_graphs(args.graphs)
         J, g = ctx.cost_grad(s)
         torch.cuda.synchronize()
         if timed:
             class_ms[classes[i]] = ctx.kernel_time()
     ctx.time_kernels("off")
+    ctx.set_graphs(args.graphs)
     dom = args.roofline_class or (max(class_ms, key=lambda c: class_ms[c][0]) if class_ms else "adj_rows")
-    if J is None:
-        J, g = ctx.cost_grad(s)
     Jw = J.cpu().numpy()
     if not np.all(np.isfinite(Jw)):
         raise RuntimeError(f"non-finite cost in warm-up: {Jw}")
 
     # timed region: K evaluations, inputs resident
-    ctx.time_kernels(dom)
     launches0 = ctx.launches
     if world > 1:
         dist.barrier()
@@ -263,8 +236,6 @@ def run_gpu(args):
         torch.cuda.nvtx.range_pop()
     ms = ev0.elapsed_time(ev1)
     launches = ctx.launches - launches0
-    dom_ms, dom_n = ctx.kernel_time()
-    ctx.time_kernels("off")
     if world > 1:
         t = torch.tensor([ms], device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -273,10 +244,25 @@ def run_gpu(args):
     units = world * B * n * n * nsteps * args.steps
     value = units / (ms / 1e3)
 
+    # roofline pass: the same evaluation with direct launches and CUDA events
+    # around every launch of the dominant pass kernel
+    ctx.time_kernels(dom)
+    rp0, rp1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rp0.record(stream)
+    for _ in range(args.roofline_evals):
+        ctx.cost_grad(s)
+    rp1.record(stream)
+    torch.cuda.synchronize()
+    dom_ms, dom_n = ctx.kernel_time()
+    roof_pass_ms = rp0.elapsed_time(rp1) / args.roofline_evals
+    ctx.time_kernels("off")
+    ctx.set_graphs(args.graphs)
+
     # end to end through the public API from pinned host memory
     s_host = s.cpu().pin_memory()
     J_host = torch.empty(B, dtype=torch.float64).pin_memory()
     g_host = torch.empty_like(s_host).pin_memory()
+    ctx.cost_grad(s_host.to(device, non_blocking=True))
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -343,6 +329,7 @@ def run_gpu(args):
         "dtype": "f64",
         "data": "synthetic (seeded spun-up Kolmogorov flow, noisy probe observations)",
         "config": {"workload": WORKLOAD_NAME, "grid": n, "nsteps": nsteps, "dt": W["dt"], "nu": W["nu"],
+                   "launch": "CUDA graph replay of each evaluation" if args.graphs else "stream launches",
                    "probes": f"{W['px']}x{W['px']} every {W['every']}", "members_per_gpu": B,
                    "kernels": [f"{k}:{a}" for k, a in kernels], "l2": "inputs larger than L2 (117 GB stage-field "
                    "trajectory streamed per evaluation)", "parallelism": f"replicas x{world}"},
@@ -352,6 +339,8 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
                      "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
                      "flops_per_launch": pf, "avg_launch_ms": avg_ms, "launches_timed": dom_n,
+                     "timed_in": "roofline pass of the same workload, direct launches, CUDA events per launch",
+                     "roofline_pass_ms_per_step": roof_pass_ms,
                      "class_ms_warmup": {k: v[0] for k, v in class_ms.items()}},
         "flops_per_gridpoint_step": flops_per_gridpoint_step(n),
         "achieved_gflops_step": value * flops_per_gridpoint_step(n) / 1e9,
@@ -418,6 +407,56 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_workload(args):
+    """Secondary workloads (one JSON line each): the adjoint-statistics
+    ensemble, the differentiable 512^2 window, Poisson-arrival serving."""
+    import torch
+
+    from paper_2602_14016_gb300 import api, build, workloads
+
+    build.build()
+    torch.cuda.set_device(0)
+    line = {"workload": args.workload, "dtype": "f64", "data": "synthetic", "n_gpus": 1}
+    if args.workload == "ensemble":
+        groups = [dict(n=256, count=args.ens256, nu=5e-4, dt=2e-3, seed0=0),
+                  dict(n=512, count=args.ens512, nu=5e-4, dt=1e-3, seed0=256)]
+        groups = [g for g in groups if g["count"] > 0]
+        res, perf = workloads.ensemble_statistics(api, torch, groups, nsteps=args.ens_steps, save_every=10,
+                                                  ckpt_every=args.ens_ckpt)
+        line.update({"metric": "fwd+adjoint gridpoint-steps/s FP64 (recompute included)", "value": perf["value"],
+                     "unit": UNIT, "seconds": perf["seconds"], "config": {"groups": groups,
+                     "nsteps": args.ens_steps, "ckpt_every": args.ens_ckpt, "save_every": 10}})
+        line["groups"] = [{"n": r["n"], "count": r["count"], "device_bytes": r["device_bytes"],
+                           "growth_rate_per_shell": [None if not np.isfinite(x) else round(float(x), 4)
+                                                     for x in r["growth_rates"][:64]],
+                           "snr_first_last": [float(r["snr"][0]), float(r["snr"][-1])],
+                           "total_mean_energy_first_last": [float(r["mean_of_energy"][0].sum()),
+                                                            float(r["mean_of_energy"][-1].sum())]}
+                          for r in res]
+    elif args.workload == "autograd":
+        out = workloads.autograd_check(api, torch, n=args.ag_n, nsteps=args.ag_steps, ckpt_every=64,
+                                       directions=args.ag_dirs)
+        line.update({"metric": "autograd gradient vs central differences", **out})
+    elif args.workload == "serve":
+        from paper_2602_14016_gb300 import serve
+
+        summary = {}
+        for rate in args.rates:
+            jobs = workloads.serving_jobs(api, torch, args.serve_jobs, rate, seed=7)
+            free = torch.cuda.mem_get_info()[0]
+            srv = serve.Server(serve.CudaExecutor(), memory_budget=int(0.6 * free), slots=args.slots,
+                               job_cap=int(0.6 * free / args.slots))
+            out = srv.run(jobs)
+            base_jobs = workloads.serving_jobs(api, torch, args.serve_jobs, rate, seed=7)
+            base = serve.Server(serve.CudaExecutor(), memory_budget=int(0.6 * free), slots=1,
+                                job_cap=int(0.6 * free / args.slots)).run(base_jobs)
+            summary[str(rate)] = {"continuous": out, "one_job_at_a_time": base}
+        line.update({"metric": "served solves/s, p50/p99 latency", "rates": summary,
+                     "config": {"jobs": args.serve_jobs, "slots": args.slots, "grids": [128, 256, 512],
+                                "horizon_steps": [200, 600], "lbfgs_iters": 5}})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -427,6 +466,20 @@ def main():
                     help="shorter window (multiple of 20) for profiling runs; the default is the workload's 2000")
     ap.add_argument("--spinup-steps", type=int, default=W["spinup_steps"])
     ap.add_argument("--roofline-class", default=None, choices=["fwd_rows", "fwd_cols", "adj_rows", "adj_cols"])
+    ap.add_argument("--roofline-evals", type=int, default=1)
+    ap.add_argument("--no-graphs", dest="graphs", action="store_false")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "autograd", "serve"],
+                    help="sweep: the headline workload above; the others print their own line")
+    ap.add_argument("--ens256", type=int, default=256)
+    ap.add_argument("--ens512", type=int, default=64)
+    ap.add_argument("--ens-steps", type=int, default=1000)
+    ap.add_argument("--ens-ckpt", type=int, default=25)
+    ap.add_argument("--ag-n", type=int, default=512)
+    ap.add_argument("--ag-steps", type=int, default=4000)
+    ap.add_argument("--ag-dirs", type=int, default=20)
+    ap.add_argument("--rates", type=float, nargs="+", default=[2.0, 10.0])
+    ap.add_argument("--serve-jobs", type=int, default=16)
+    ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-plain", dest="plain", action="store_false")
@@ -437,6 +490,8 @@ def main():
     W["spinup_steps"] = args.spinup_steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "sweep":
+        run_workload(args)
     else:
         run_gpu(args)
 

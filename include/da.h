@@ -159,6 +159,15 @@ da_status da_cost_grad(da_ctx* ctx, const double* s, double* J, double* grad_s, 
  * checkpoints, a second da_vjp needs a new da_forward. */
 da_status da_vjp(da_ctx* ctx, const double* dobs, const double* dwT, double* grad_s, void* stream);
 
+/* enable != 0: da_cost_grad (and so da_assimilate) captures its whole launch
+ * sequence into a CUDA graph on the first call and replays it afterwards on
+ * an internal stream, ordered after and before the caller's stream by
+ * events; the control is copied into and the gradient out of internal
+ * buffers.  For small grids this removes the per-launch host cost.  The
+ * capture is redone after da_set_sobolev; kernel timing (da_time_kernels)
+ * bypasses the graph.  The first call must not itself be inside a capture. */
+da_status da_set_graphs(da_ctx* ctx, int enable);
+
 /* Optional extra outputs of the last da_cost_grad / da_adjoint_terminal on
  * this context: lam0 [batch][n][n/2+1] complex, the DFT of grad_{w0} J
  * (the physical adjoint at t = 0, Eq. 12); filtered [batch][n][n] the

@@ -110,6 +110,10 @@ class Context:
         """Regularisation lambda/2 sum |grad u0|^2 of Eq. (4) (0: off)."""
         self._check(self.lib.da_set_sobolev(self.ctx, float(lam)))
 
+    def set_graphs(self, enable: bool = True):
+        """Replay da_cost_grad as a captured CUDA graph."""
+        self._check(self.lib.da_set_graphs(self.ctx, int(enable)))
+
     def set_observations(self, m: torch.Tensor, stream=None):
         m = m.to(self.device, torch.float64).contiguous()
         assert m.numel() == self.cfg.batch * self.nt * self.cfg.px ** 2 * 2

@@ -48,6 +48,13 @@ struct da_ctx {
   double *part = nullptr, *dots = nullptr, *scal = nullptr;
   void** ptrs = nullptr;
   int mem = 0;
+  // CUDA-graph replay of da_cost_grad
+  bool use_graph = false;
+  cudaGraphExec_t cg_exec = nullptr;
+  unsigned long long cg_launches = 0;  // kernel nodes in the captured graph
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  double *sbuf = nullptr, *gbuf = nullptr;
   // event timing of one kernel class
   int timed_class = 0;
   std::vector<cudaEvent_t> ev;
@@ -281,7 +288,7 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
 
 extern "C" da_status da_time_kernels(da_ctx* c, int kernel_class) {
   if (!c || kernel_class < 0 || kernel_class > 4) return fail(c, DA_EINVAL, "kernel_class must be in [0, 4]");
-  c->timed_class = kernel_class;
+  c->timed_class = kernel_class;  // while on, da_cost_grad launches directly, not by graph
   c->ev_used = 0;
   return DA_OK;
 }
@@ -303,6 +310,10 @@ extern "C" da_status da_kernel_time(da_ctx* c, double* total_ms, unsigned long l
 
 extern "C" void da_destroy(da_ctx* c) {
   if (!c) return;
+  if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   delete c;
@@ -320,6 +331,10 @@ extern "C" da_status da_set_sobolev(da_ctx* c, double lambda) {
     if (r) return r;
   }
   c->sobolev = lambda;
+  if (c->cg_exec) {  // the captured sequence depends on the regularisation
+    cudaGraphExecDestroy(c->cg_exec);
+    c->cg_exec = nullptr;
+  }
   return DA_OK;
 }
 
@@ -499,11 +514,8 @@ extern "C" da_status da_forward(da_ctx* c, const double* s, double* omegaT, doub
   return DA_OK;
 }
 
-extern "C" da_status da_cost_grad(da_ctx* c, const double* s, double* J, double* grad_s, void* stream) {
-  if (!c || !s) return fail(c, DA_EINVAL, "ctx and s must not be NULL");
-  if (!c->have_obs) return fail(c, DA_EINVAL, "no observations: call da_set_observations first");
-  if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
-  cudaStream_t st = (cudaStream_t)stream;
+// The launch sequence of one cost-and-gradient evaluation, on stream st.
+static da_status enqueue_cost_grad(da_ctx* c, const double* s, double* grad_s, cudaStream_t st) {
   da_status r = run_forward(c, s, true, st);
   if (r) return r;
   da::k_residual<<<c->B, 256, 0, st>>>(c->dev);
@@ -519,8 +531,71 @@ extern "C" da_status da_cost_grad(da_ctx* c, const double* s, double* J, double*
     da::k_sobolev_grad<<<(count + 255) / 256, 256, 0, st>>>(c->dev.LamBar, c->w0, c->sobolev, count);
     if ((r = check_launch(c))) return r;
   }
+  return gradient_out(c, grad_s, st);
+}
+
+extern "C" da_status da_set_graphs(da_ctx* c, int enable) {
+  if (!c) return fail(c, DA_EINVAL, "ctx must not be NULL");
+  if (!enable) {
+    c->use_graph = false;
+    return DA_OK;
+  }
+  if (!c->gstream) {
+    const size_t len = (size_t)c->B * c->n * c->n;
+    da_status r = dalloc(c, &c->sbuf, len);
+    if (!r) r = dalloc(c, &c->gbuf, len);
+    if (r) return r;
+    DA_TRY_CUDA(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    DA_TRY_CUDA(c, cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    DA_TRY_CUDA(c, cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+  }
+  c->use_graph = true;
+  return DA_OK;
+}
+
+extern "C" da_status da_cost_grad(da_ctx* c, const double* s, double* J, double* grad_s, void* stream) {
+  if (!c || !s) return fail(c, DA_EINVAL, "ctx and s must not be NULL");
+  if (!c->have_obs) return fail(c, DA_EINVAL, "no observations: call da_set_observations first");
+  if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
+  cudaStream_t st = (cudaStream_t)stream;
+  da_status r;
+  if (c->use_graph && c->timed_class == 0) {
+    // replay one captured evaluation on the context's stream, ordered after
+    // and before the caller's stream by events
+    const size_t bytes = (size_t)c->B * c->n * c->n * sizeof(double);
+    DA_TRY_CUDA(c, cudaMemcpyAsync(c->sbuf, s, bytes, cudaMemcpyDeviceToDevice, st));
+    DA_TRY_CUDA(c, cudaEventRecord(c->ev_in, st));
+    DA_TRY_CUDA(c, cudaStreamWaitEvent(c->gstream, c->ev_in, 0));
+    if (!c->cg_exec) {
+      cudaGraph_t g = nullptr;
+      const unsigned long long l0 = c->launches;
+      DA_TRY_CUDA(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+      r = enqueue_cost_grad(c, c->sbuf, c->gbuf, c->gstream);
+      cudaError_t e = cudaStreamEndCapture(c->gstream, &g);
+      if (r) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      if (e != cudaSuccess) return fail(c, DA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&c->cg_exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        c->cg_exec = nullptr;
+        return fail(c, DA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      }
+      c->cg_launches = c->launches - l0;
+      c->launches = l0;
+    }
+    DA_TRY_CUDA(c, cudaGraphLaunch(c->cg_exec, c->gstream));
+    c->launches += c->cg_launches;
+    c->have_fwd = c->ckpt == 0;
+    DA_TRY_CUDA(c, cudaEventRecord(c->ev_out, c->gstream));
+    DA_TRY_CUDA(c, cudaStreamWaitEvent(st, c->ev_out, 0));
+    if (grad_s) DA_TRY_CUDA(c, cudaMemcpyAsync(grad_s, c->gbuf, bytes, cudaMemcpyDeviceToDevice, st));
+  } else {
+    if ((r = enqueue_cost_grad(c, s, grad_s, st))) return r;
+  }
   c->have_adj = true;
-  if ((r = gradient_out(c, grad_s, st))) return r;
   return copy_scalars_out(c, J, st);
 }
 

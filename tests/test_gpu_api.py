@@ -72,3 +72,23 @@ def test_bitwise_deterministic(api):
     J1, g1 = ctx.cost_grad(s * 0.9)
     J2, g2 = ctx.cost_grad(s * 0.9)
     assert torch.equal(J1, J2) and torch.equal(g1, g2)
+
+
+@pytest.mark.parametrize("ckpt", [0, 3])
+def test_graph_replay_equals_direct_launches(api, ckpt):
+    cfg = small(api, kernels=[api.KernelSpec("frac", 0.5), api.KernelSpec("exp_abs", 0.3)], ckpt_every=ckpt)
+    direct, graph = api.Context(cfg), api.Context(cfg)
+    graph.set_graphs(True)
+    w = np.stack([synthetic.random_vorticity_hat(32, 7), synthetic.random_vorticity_hat(32, 8)])
+    s = direct.control_from_omega(torch.from_numpy(w).cuda())
+    _, m = direct.forward(s)
+    for c in (direct, graph):
+        c.set_observations(m * 1.02)
+    for scale in (0.9, 1.1, 0.95):  # several replays with different controls
+        J1, g1 = direct.cost_grad(s * scale)
+        J2, g2 = graph.cost_grad(s * scale)
+        assert torch.equal(J1, J2) and torch.equal(g1, g2)
+    s1, s2 = (s * 0.9).contiguous(), (s * 0.9).contiguous()
+    H1, i1, _ = direct.assimilate(s1, 3)
+    H2, i2, _ = graph.assimilate(s2, 3)
+    assert np.array_equal(H1, H2) and np.array_equal(i1, i2) and torch.equal(s1, s2)
