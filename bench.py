@@ -173,11 +173,9 @@ def run_gpu(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2602_14016_gb300 import api, build
+    from paper_2602_14016_gb300 import api, build, replicas
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, local, world = replicas.env_world()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -236,13 +234,11 @@ def run_gpu(args):
         torch.cuda.nvtx.range_pop()
     ms = ev0.elapsed_time(ev1)
     launches = ctx.launches - launches0
+    # whole job: the units of every rank over the slowest rank's time
+    value = replicas.whole_job_rate(B * n * n * nsteps * args.steps, ms / 1e3, device)
+    ms = replicas.max_over_ranks(ms, device)
     if world > 1:
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    units = world * B * n * n * nsteps * args.steps
-    value = units / (ms / 1e3)
 
     # roofline pass: the same evaluation with direct launches and CUDA events
     # around every launch of the dominant pass kernel
@@ -277,11 +273,7 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
-    e2e_value = world * B * n * n * nsteps * e_steps / (e_ms / 1e3)
+    e2e_value = replicas.whole_job_rate(B * n * n * nsteps * e_steps, e_ms / 1e3, device)
 
     # the plain one-job-per-launch path: the same members one at a time
     plain = None

@@ -86,3 +86,23 @@ def test_hbm_use_shrinks_with_checkpoints(orc, mods):
     cfg.ckpt_every = 8
     ck = api.Context(cfg)
     assert ck.device_bytes < full.device_bytes / 4
+
+
+def test_kolmogorov_copy_at_64_against_oracle(orc, mods):
+    """A 64^2 copy of the differentiable Kolmogorov window (checkpoints every
+    8 steps): the autograd gradient of the misfit equals the oracle's."""
+    api, ag = mods
+    probs, cfg = make_pair(orc, 64, 48, 1e-3 * 4, 1 / 200, kernels=[("frac", 0.5)], px=16, every=8,
+                           forcing="kolmogorov", nf=4)
+    cfg.ckpt_every = 8
+    P = probs[0]
+    truth, guess = truth_and_guess(orc, P, 130, 131, scale=2.0)
+    _, m = orc.forward(P, truth)
+    J, g, _ = orc.cost_grad(P, guess, m)
+    ctx = api.Context(cfg)
+    s = cu(guess[None]).requires_grad_(True)
+    obs, _ = ag.solve(s, ctx)
+    L = ag.misfit(obs, cu(m[None])).sum()
+    L.backward()
+    assert abs(L.item() - J) <= 1e-12 * J
+    assert rel(s.grad.cpu().numpy()[0], g) < 1e-8
