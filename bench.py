@@ -13,7 +13,7 @@ of the sweep |k|^(-2s), s in {0, 0.5, 1, 1.5}, and exp(-a|k|), a in
 Metric: fwd+adjoint gridpoint-steps/s (FP64) = members x n^2 x nsteps per
 evaluation / time.  The timed region holds K evaluations with the inputs
 resident on the device; the stage-field trajectory of an evaluation
-(117 GB) is far larger than L2, so no flush is needed.  `e2e` repeats the
+(58.7 GB) is far larger than L2, so no flush is needed.  `e2e` repeats the
 measurement through the public API from pinned host memory (controls in,
 cost and gradient out).  `--impl reference` times the CPU oracle on a
 bounded sample of the same workload.  Under torchrun each rank runs its
@@ -72,11 +72,14 @@ def pass_flops(n: int, batch: int) -> dict:
     K = (n - 1) // 3
     Kc, Kr = K + 1, 2 * K + 1
     f = fft_flops(n)
+    # rows: two packed complex transforms per row (inverse of u + i v, or of
+    # the adjoint fields a + i b, and forward of the two products); columns:
+    # two forward and two inverse transforms per retained column kx
     return {
-        "fwd_rows": batch * (2.5 * n * f + 3.0 * n * n),
-        "fwd_cols": batch * (5.0 * Kc * f + 24.0 * Kr * Kc),
-        "adj_rows": batch * (2.5 * n * f + 4.0 * n * n),
-        "adj_cols": batch * (5.0 * Kc * f + 34.0 * Kr * Kc),
+        "fwd_rows": batch * (2.0 * n * f + 4.0 * n * n),
+        "fwd_cols": batch * (4.0 * Kc * f + 26.0 * Kr * Kc),
+        "adj_rows": batch * (2.0 * n * f + 8.0 * n * n),
+        "adj_cols": batch * (4.0 * Kc * f + 32.0 * Kr * Kc),
     }
 
 
@@ -323,7 +326,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD_NAME, "grid": n, "nsteps": nsteps, "dt": W["dt"], "nu": W["nu"],
                    "launch": "CUDA graph replay of each evaluation" if args.graphs else "stream launches",
                    "probes": f"{W['px']}x{W['px']} every {W['every']}", "members_per_gpu": B,
-                   "kernels": [f"{k}:{a}" for k, a in kernels], "l2": "inputs larger than L2 (117 GB stage-field "
+                   "kernels": [f"{k}:{a}" for k, a in kernels], "l2": "inputs larger than L2 (58.7 GB stage-field "
                    "trajectory streamed per evaluation)", "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(s_host.numel() * 8),
                 "d2h_bytes_per_step": int(J_host.numel() * 8 + g_host.numel() * 8)},

@@ -62,7 +62,8 @@ typedef enum {
 /* Grid and time window.  n: points per side, a power of two in [16, 1024].
  * L: domain side, must be 2 pi (0 means 2 pi).  dt, nsteps: RK4 step and
  * count.  ckpt_every: 0 stores every stage field of every step for the
- * adjoint (the default; 128 n^2 bytes per step per member); K > 0 keeps the
+ * adjoint (the default; 64 n^2 bytes per step per member: u, v of the four
+ * RK stages); K > 0 keeps the
  * state every K steps and the stage fields of one K-step segment, and the
  * adjoint recomputes each segment from its checkpoint (one extra forward
  * solve; results are bitwise those of full storage); -1 keeps nothing

@@ -212,8 +212,8 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
   A(dalloc(c, &d.KB, comp));
   A(dalloc(c, &d.LamBar, comp));
   A(dalloc(c, &d.Sum, comp));
-  A(dalloc(c, &d.Mx, B * 4 * N * ops->Kc));
-  A(dalloc(c, &d.Mn, B * N * ops->Kc));
+  A(dalloc(c, &d.Mx, B * 2 * N * ops->Kc));
+  A(dalloc(c, &d.Mn, B * 2 * N * ops->Kc));
   A(dalloc(c, &d.obs, B * c->nt * P2 * 2));
   A(dalloc(c, (double**)&d.mobs, B * c->nt * P2 * 2));
   A(dalloc(c, &d.res, B * c->nt * P2 * 2));
@@ -229,7 +229,7 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
     c->nckpt = (c->nsteps + c->ckpt - 1) / c->ckpt;
     A(dalloc(c, &c->ckpt_buf, (size_t)c->nckpt * comp));
   }
-  if (c->ckpt >= 0) A(dalloc(c, &d.traj, B * (size_t)d.traj_steps * 16 * N * N));
+  if (c->ckpt >= 0) A(dalloc(c, &d.traj, B * (size_t)d.traj_steps * 8 * N * N));
   int* d_kind = nullptr;
   double *d_param = nullptr, *d_table = nullptr;
   A(dalloc(c, &d_kind, B));
@@ -422,11 +422,11 @@ static da_status record_spectra(da_ctx* c, const SpectraOut* sp, int k, cudaStre
   return DA_OK;
 }
 
-// Backward sweep from the state in LamBar/KB/Mn (set by adj_init), segment by
+// Backward sweep from the state in LamBar/KB/Mx (set by adj_init), segment by
 // segment from the last.  With checkpoints, every segment but the last is
 // first recomputed from its checkpoint (bitwise the same stage fields as the
-// first pass), then the inverse column transform of kbar, which the forward
-// recompute overwrote, is redone.
+// first pass), then the inverse column transforms of the adjoint fields of
+// kbar, which the forward recompute overwrote, are redone.
 static da_status run_adjoint(da_ctx* c, bool sources, cudaStream_t st, const SpectraOut* sp = nullptr) {
   const Ops* o = c->ops;
   Dev& d = c->dev;
@@ -453,7 +453,7 @@ static da_status run_adjoint(da_ctx* c, bool sources, cudaStream_t st, const Spe
         }
         if ((r = check_launch(c, 8))) return r;
       }
-      o->spec_to_mixed(d, d.KB, da::M_ONE, st);
+      o->adj_init(d, da::INIT_RESUME, st);
       if ((r = check_launch(c))) return r;
     }
     d.seg0 = k0;

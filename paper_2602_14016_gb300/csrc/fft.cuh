@@ -134,69 +134,67 @@ __device__ __forceinline__ void dftR(double2* a) {
 template <int... Rs>
 struct Radices {};
 
-// Plan for four concurrent transforms (the widest radices keep the
-// instruction count lowest) and for a single transform (radices small enough
-// that every stage fills whole warps, so no lane idles in the FP64 pipe).
+// Plan for two concurrent transforms (the pass kernels) and for a single
+// transform (control and gradient maps), with the CTA width they run on.
+// Wide radices keep the FP64 instruction count low; the width is chosen so
+// that the stages of the two-transform plan fill whole warps (a stage with
+// more butterflies than threads gives each thread several).
 template <int N> struct Plan;
-template <> struct Plan<16> { using four = Radices<4, 4>; using one = Radices<4, 4>; };
-template <> struct Plan<32> { using four = Radices<4, 8>; using one = Radices<4, 8>; };
-template <> struct Plan<64> { using four = Radices<8, 8>; using one = Radices<4, 4, 4>; };
-template <> struct Plan<128> { using four = Radices<8, 16>; using one = Radices<4, 4, 8>; };
-template <> struct Plan<256> { using four = Radices<16, 16>; using one = Radices<8, 8, 4>; };
-template <> struct Plan<512> { using four = Radices<8, 8, 8>; using one = Radices<8, 8, 8>; };
-template <> struct Plan<1024> { using four = Radices<16, 8, 8>; using one = Radices<16, 8, 8>; };
-
-template <typename P> struct MinRadix;
-template <int R> struct MinRadix<Radices<R>> { static constexpr int value = R; };
-template <int R, int... Rs> struct MinRadix<Radices<R, Rs...>> {
-  static constexpr int rest = MinRadix<Radices<Rs...>>::value;
-  static constexpr int value = R < rest ? R : rest;
-};
+template <> struct Plan<16> { using two = Radices<4, 4>; using one = Radices<4, 4>; static constexpr int threads = 32; };
+template <> struct Plan<32> { using two = Radices<4, 8>; using one = Radices<4, 8>; static constexpr int threads = 32; };
+template <> struct Plan<64> { using two = Radices<4, 4, 4>; using one = Radices<4, 4, 4>; static constexpr int threads = 32; };
+template <> struct Plan<128> { using two = Radices<4, 4, 8>; using one = Radices<4, 4, 8>; static constexpr int threads = 64; };
+template <> struct Plan<256> { using two = Radices<8, 8, 4>; using one = Radices<8, 8, 4>; static constexpr int threads = 64; };
+template <> struct Plan<512> { using two = Radices<8, 8, 8>; using one = Radices<8, 8, 8>; static constexpr int threads = 128; };
+template <> struct Plan<1024> { using two = Radices<16, 8, 8>; using one = Radices<16, 8, 8>; static constexpr int threads = 256; };
 
 template <int N>
 struct PlanInfo {
-  // threads that give every butterfly of four concurrent transforms (and of
-  // one transform) its own thread
-  static constexpr int T4 = 4 * N / MinRadix<typename Plan<N>::four>::value;
-  static constexpr int T1 = N / MinRadix<typename Plan<N>::one>::value;
-  static constexpr int TM = T4 > T1 ? T4 : T1;
-  static constexpr int THREADS = TM < 32 ? 32 : TM;
+  static constexpr int THREADS = Plan<N>::threads;
 };
 
 // One in-place Stockham stage on F sequences of N points stored back to back
-// in `buf`: every thread loads the R points of its butterfly, twiddles and
-// transforms them in registers, waits for all loads, then stores.
+// in `buf`: every thread loads the R points of each of its butterflies,
+// twiddles and transforms them in registers, waits for all loads, then
+// stores.
 template <int N, int R, int S, int F>
 __device__ __forceinline__ void stockham_stage(double2* buf, int L, const double2* __restrict__ tw) {
-  constexpr int NB = N / R;
-  static_assert(F * NB <= PlanInfo<N>::THREADS, "one butterfly per thread");
-  const int u = threadIdx.x;
-  const bool active = u < F * NB;
-  double2 a[R];
-  int base = 0, j = 0;
-  if (active) {
-    const int f = u / NB;
-    const int i = u - f * NB;
-    const int k = i & (L - 1);
-    base = f * N;
+  constexpr int NB = N / R, T = PlanInfo<N>::THREADS, TOT = F * NB, J = (TOT + T - 1) / T;
+  double2 a[J][R];
+  int base[J], dst[J];
 #pragma unroll
-    for (int m = 0; m < R; ++m) a[m] = buf[base + i + m * NB];
-    if (L > 1) {
-      const int step = N / (L * R);
+  for (int jb = 0; jb < J; ++jb) {
+    const int u = threadIdx.x + jb * T;
+    base[jb] = 0;
+    dst[jb] = 0;
+    if (TOT % T == 0 || u < TOT) {
+      const int f = u / NB;
+      const int i = u - f * NB;
+      const int k = i & (L - 1);
+      base[jb] = f * N;
 #pragma unroll
-      for (int m = 1; m < R; ++m) {
-        double2 w = tw[m * k * step];
-        if (S > 0) w.y = -w.y;
-        a[m] = cmul(a[m], w);
+      for (int m = 0; m < R; ++m) a[jb][m] = buf[base[jb] + i + m * NB];
+      if (L > 1) {
+        const int step = N / (L * R);
+#pragma unroll
+        for (int m = 1; m < R; ++m) {
+          double2 w = tw[m * k * step];
+          if (S > 0) w.y = -w.y;
+          a[jb][m] = cmul(a[jb][m], w);
+        }
       }
+      dftR<R, S>(a[jb]);
+      dst[jb] = (i - k) * R + k;
     }
-    dftR<R, S>(a);
-    j = (i - k) * R + k;
   }
   __syncthreads();
-  if (active) {
 #pragma unroll
-    for (int m = 0; m < R; ++m) buf[base + j + m * L] = a[m];
+  for (int jb = 0; jb < J; ++jb) {
+    const int u = threadIdx.x + jb * T;
+    if (TOT % T == 0 || u < TOT) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) buf[base[jb] + dst[jb] + m * L] = a[jb][m];
+    }
   }
   __syncthreads();
 }
@@ -210,16 +208,16 @@ __device__ __forceinline__ void run_stages(double2* buf, const double2* tw, Radi
   run_stages<N, S, F, L * R>(buf, tw, Radices<Rs...>{});
 }
 
-// Transform, in place, F (1 or 4) sequences of N points stored back to back
+// Transform, in place, F (1 or 2) sequences of N points stored back to back
 // in buf.  Called by every thread of a CTA of PlanInfo<N>::THREADS threads,
 // with buf already synchronised; returns after a final __syncthreads().
 template <int N, int S, int F>
 __device__ __forceinline__ void fft_batch(double2* buf, const double2* tw) {
-  static_assert(F == 1 || F == 4, "batches of one or four transforms");
+  static_assert(F == 1 || F == 2, "batches of one or two transforms");
   if constexpr (F == 1)
     run_stages<N, S, F, 1>(buf, tw, typename Plan<N>::one{});
   else
-    run_stages<N, S, F, 1>(buf, tw, typename Plan<N>::four{});
+    run_stages<N, S, F, 1>(buf, tw, typename Plan<N>::two{});
 }
 
 }  // namespace da

@@ -4,22 +4,30 @@
 //   compact spectra  [Kr][Kc] complex: the retained set of the 2/3 rule,
 //                    kx = 0..K (columns), compact row r -> ky = r (r <= K)
 //                    or r - Kr; K = floor((N-1)/3), Kc = K+1, Kr = 2K+1.
-//   mixed fields     [N][Kc] complex: physical y, spectral kx (the transform
-//                    along y of a compact column).
-//   stage fields     [nsteps][4 stages][4 fields][N][N] double: u, v,
-//                    dw/dx, dw/dy of every RK stage state, written by the
-//                    forward row pass and read back by the adjoint row pass.
+//   mixed fields     [2][N][Kc] complex: physical y, spectral kx (the
+//                    transform along y of a compact column), two fields.
+//   stage fields     [nsteps][4 stages][2 fields][N][N] double: u, v of
+//                    every RK stage state, written by the forward row pass
+//                    and read back by the adjoint row pass.
+//
+// The advection term is evaluated in the divergence form of Basdevant
+// (1983): for a divergence-free band-limited velocity,
+//   u . grad w = (d_xx - d_yy)(u v) + d_xy (v^2 - u^2),
+// and with the 2/3 rule both sides are the same retained coefficients (the
+// products of retained fields alias nothing onto the retained set), so the
+// discrete right-hand side is the one of the advective form, u w_x + v w_y,
+// evaluated with four real transforms instead of five and two stored stage
+// fields instead of four.
 //
 // A forward RK stage is two kernels: a ROW pass (inverse transforms along x
-// of the packed mixed rows -> u, v, w_x, w_y; stage-field store; probe
-// gather; product u w_x + v w_y; forward transform along x of two rows
-// packed as one complex sequence) and a COLUMN pass (forward transform along
-// y of the product, RK epilogue with viscosity, forcing and the stage
-// update, then the four inverse column transforms of the next stage's
-// velocity and vorticity gradient).  The adjoint mirrors this with the
-// transposed operators.  Every transform is an FP64 shared-memory FFT from
-// fft.cuh; the 1/N^2 of the inverse 2D transform is applied once, to the
-// spectral coefficients before the column transform.
+// of the packed mixed rows -> u, v; stage-field store; probe gather; the
+// products u v and v^2 - u^2; their forward transforms along x) and a COLUMN
+// pass (forward transforms along y of the two products, the advection term,
+// RK epilogue with viscosity, forcing and the stage update, then the
+// inverse column transforms of the next stage's u and v).  The adjoint
+// mirrors this with the transposed operators.  Every transform is an FP64
+// shared-memory FFT from fft.cuh; the 1/N^2 of the inverse 2D transform is
+// applied once, to the spectral coefficients before the column transform.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -38,8 +46,9 @@ enum : int {
 };
 
 // Start of the adjoint sweep (k_adj_init): add the observation source of
-// the last step, and/or start from the terminal field already in LamBar.
-enum : int { INIT_SRC = 1, INIT_LAMBAR = 2 };
+// the last step, and/or start from the terminal field already in LamBar; or
+// resume from the adjoint stage value in KB after a checkpoint recompute.
+enum : int { INIT_SRC = 1, INIT_LAMBAR = 2, INIT_RESUME = 4 };
 
 // Multipliers of the generic spectral-to-mixed column pass.
 enum : int { M_ONE = 0, M_CTRL = 1, M_FILTERED = 2, M_INV_CTRL = 3 };
@@ -52,9 +61,9 @@ struct Dev {
   double amp;
   int nf;
   double2 *W, *Acc, *Y, *KB, *LamBar, *Sum;  // compact [B][Kr][Kc]
-  double2* Mx;                               // mixed [B][4][N][Kc]
-  double2* Mn;                               // mixed [B][N][Kc]
-  double* traj;                              // [B][traj_steps][4][4][N][N]
+  double2* Mx;                               // mixed [B][2][N][Kc]: column-pass output
+  double2* Mn;                               // mixed [B][2][N][Kc]: row-pass output
+  double* traj;                              // [B][traj_steps][4][2][N][N]
   int traj_steps;                            // steps the stage-field store holds
   int seg0;                                  // step stored in slot 0 of the store
   double* obs;                               // model observations [B][nt][P2][2]
@@ -72,11 +81,11 @@ struct Geo {
   static constexpr int Kc = K + 1;
   static constexpr int Kr = 2 * K + 1;
   static constexpr int NH = N / 2 + 1;
-  // threads: four transforms at a time, one butterfly of each stage per thread
+  // threads: two transforms at a time (fft.cuh)
   static constexpr int THREADS = PlanInfo<N>::THREADS;
-  // shared memory: twiddles + one buffer of four sequences + probe sums
+  // shared memory: twiddles + one buffer of two sequences + probe sums
   static constexpr int PMAX = 64;
-  static constexpr size_t SMEM = sizeof(double2) * (N + 4 * N + 2 * PMAX);
+  static constexpr size_t SMEM = sizeof(double2) * (N + 2 * N + 2 * PMAX);
 };
 
 __device__ __forceinline__ int ky_of_row(int r, int K) { return r <= K ? r : r - (2 * K + 1); }
@@ -166,7 +175,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_r2c_rows(Dev d, const doubl
   for (int x = threadIdx.x; x < N; x += G::THREADS) a[x] = make_double2(r0[x], r0[N + x]);
   __syncthreads();
   fft_batch<N, -1, 1>(a, tw);
-  double2* M = d.Mn + ((size_t)bm * N + y0) * G::Kc;
+  double2* M = d.Mn + ((size_t)bm * 2 * N + y0) * G::Kc;
   #pragma unroll
   for (int kx = threadIdx.x; kx < G::Kc; kx += G::THREADS) {
     double2 A, Bv;
@@ -185,7 +194,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_c2r_rows(Dev d, double* __r
   double2 *tw = sm, *a = tw + N;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
   load_twiddles<N>(tw, d.tw);
-  const double2* M = d.Mn + ((size_t)bm * N + y0) * G::Kc;
+  const double2* M = d.Mn + ((size_t)bm * 2 * N + y0) * G::Kc;
   pack_rows<N, G::THREADS>(a, M, M + G::Kc);
   __syncthreads();
   fft_batch<N, +1, 1>(a, tw);
@@ -198,7 +207,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_c2r_rows(Dev d, double* __r
 }
 
 // Compact spectrum src[b] times a multiplier (and 1/N^2), transformed along
-// y -> mixed Mn[b].  grid (Kc, B).
+// y -> mixed Mn[b] (first field).  grid (Kc, B).
 template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_spec_to_mixed(Dev d, const double2* __restrict__ src, int mode) {
   using G = Geo<N>;
@@ -226,7 +235,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_spec_to_mixed(Dev d, const 
   }
   __syncthreads();
   fft_batch<N, +1, 1>(a, tw);
-  double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
+  double2* M = d.Mn + (size_t)bm * 2 * N * G::Kc + kx;
   #pragma unroll
   for (int y = threadIdx.x; y < N; y += G::THREADS) M[(size_t)y * G::Kc] = a[y];
 }
@@ -260,11 +269,12 @@ __global__ void k_half_to_compact(const double2* __restrict__ in, double2* __res
 }
 
 // ---------------------------------------------------------------------------
-// Control map and the four inverse column transforms of a stage state
+// Control map and the inverse column transforms of a stage state
 // ---------------------------------------------------------------------------
 
-// Writes the four column values (u, v, w_x, w_y of state value Yv at ky,
-// column kx, scaled by 1/N^2) into position q = ky mod N of seq[0..3][N].
+// Writes the two column values (u = i ky/k^2 w, v = -i kx/k^2 w of state
+// value Yv at ky, column kx, scaled by 1/N^2) into position q = ky mod N of
+// seq[0..1][N].
 template <int N>
 __device__ __forceinline__ void put_stage_columns(double2* seq, int kx, int ky, double2 Yv) {
   const double k2 = (double)(kx * kx + ky * ky);
@@ -273,10 +283,20 @@ __device__ __forceinline__ void put_stage_columns(double2* seq, int kx, int ky, 
   const int q = ky & (N - 1);
   const double2 Ys = cscale(Yv, s);
   const double a = ky * ik2, c = kx * ik2;
-  seq[q] = make_double2(-a * Ys.y, a * Ys.x);                  // u:  i ky / k^2
-  seq[N + q] = make_double2(c * Ys.y, -c * Ys.x);              // v: -i kx / k^2
-  seq[2 * N + q] = make_double2(-kx * Ys.y, kx * Ys.x);        // w_x: i kx
-  seq[3 * N + q] = make_double2(-ky * Ys.y, ky * Ys.x);        // w_y: i ky
+  seq[q] = make_double2(-a * Ys.y, a * Ys.x);      // u:  i ky / k^2
+  seq[N + q] = make_double2(c * Ys.y, -c * Ys.x);  // v: -i kx / k^2
+}
+
+// Writes the two column values of the adjoint fields of an adjoint stage
+// value kb: a = d_xy kb = -kx ky kb and b = (d_xx - d_yy) kb =
+// (ky^2 - kx^2) kb, scaled by 1/N^2, at q = ky mod N of seq[0..1][N].
+template <int N>
+__device__ __forceinline__ void put_adjoint_columns(double2* seq, int kx, int ky, double2 kb) {
+  const double s = 1.0 / ((double)N * N);
+  const int q = ky & (N - 1);
+  const double ca = -(double)(kx * ky) * s, cb = (double)(ky * ky - kx * kx) * s;
+  seq[q] = cscale(kb, ca);
+  seq[N + q] = cscale(kb, cb);
 }
 
 // Zeroes the positions outside the retained set in `nseq` sequences.
@@ -289,14 +309,15 @@ __device__ __forceinline__ void zero_outside(double2* seq, int nseq) {
   }
 }
 
+// The two transformed columns of seq -> column kx of both fields of Mx[bm].
 template <int N>
-__device__ __forceinline__ void store_mixed4(const Dev& d, const double2* z, int bm, int kx) {
+__device__ __forceinline__ void store_mixed2(const Dev& d, const double2* z, int bm, int kx) {
   using G = Geo<N>;
-  double2* M = d.Mx + (size_t)bm * 4 * N * G::Kc + kx;
+  double2* M = d.Mx + (size_t)bm * 2 * N * G::Kc + kx;
 #pragma unroll
-  for (int t = 0; t < (4 * N + G::THREADS - 1) / G::THREADS; ++t) {
+  for (int t = 0; t < (2 * N + G::THREADS - 1) / G::THREADS; ++t) {
     const int u = threadIdx.x + t * G::THREADS;
-    if (u < 4 * N) M[(size_t)u * G::Kc] = z[u];
+    if (u < 2 * N) M[(size_t)u * G::Kc] = z[u];
   }
 }
 
@@ -312,9 +333,39 @@ __device__ __forceinline__ void load_column(double2* seq, const double2* __restr
   }
 }
 
+// Both rows y0, y0+1 of the two fields of a mixed buffer, packed for the
+// inverse transform along x: sequence rr holds row y0+rr of (field 0,
+// field 1) as field0 + i field1.
+template <int N>
+__device__ __forceinline__ void pack_field_pairs(double2* a, const double2* __restrict__ M, int y0) {
+  constexpr int Kc = Geo<N>::Kc;
+#pragma unroll
+  for (int rr = 0; rr < 2; ++rr)
+    pack_rows<N, Geo<N>::THREADS>(a + rr * N, M + (size_t)(y0 + rr) * Kc, M + ((size_t)N + y0 + rr) * Kc);
+}
+
+// Forward transforms along x of rows y0, y0+1 of two real fields, packed as
+// seq f = (field f row y0) + i (field f row y0+1) -> rows of both fields of
+// the mixed buffer O (kx <= K).
+template <int N>
+__device__ __forceinline__ void unpack_field_rows(const double2* a, double2* __restrict__ O, int y0) {
+  using G = Geo<N>;
+#pragma unroll
+  for (int t = 0; t < (2 * G::Kc + G::THREADS - 1) / G::THREADS; ++t) {
+    const int u = threadIdx.x + t * G::THREADS;
+    if (u < 2 * G::Kc) {
+      const int f = u / G::Kc, kx = u - f * G::Kc;
+      double2 A, Bv;
+      unpack_pair<N>(a + f * N, kx, A, Bv);
+      O[((size_t)f * N + y0) * G::Kc + kx] = A;
+      O[((size_t)f * N + y0 + 1) * G::Kc + kx] = Bv;
+    }
+  }
+}
+
 // s_hat = forward transform along y of the mixed rows in Mn; w0 = mult s_hat
-// into W (and Y); then, unless F_NO_NEXT, the four inverse column transforms
-// of stage 1.  grid (Kc, B).
+// into W (and Y); then, unless F_NO_NEXT, the inverse column transforms of
+// u and v of stage 1.  grid (Kc, B).
 template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_ctrl_cols(Dev d, int flags) {
   using G = Geo<N>;
@@ -322,7 +373,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_ctrl_cols(Dev d, int flags)
   double2 *tw = sm, *a = tw + N;
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
-  const double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
+  const double2* M = d.Mn + (size_t)bm * 2 * N * G::Kc + kx;
   load_column<N, G::THREADS, 1>(a, M);
   __syncthreads();
   fft_batch<N, -1, 1>(a, tw);
@@ -337,14 +388,14 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_ctrl_cols(Dev d, int flags)
     put_stage_columns<N>(a, kx, ky, w0);
   }
   if (flags & F_NO_NEXT) return;
-  zero_outside<N>(a, 4);
+  zero_outside<N>(a, 2);
   __syncthreads();
-  fft_batch<N, +1, 4>(a, tw);
-  store_mixed4<N>(d, a, bm, kx);
+  fft_batch<N, +1, 2>(a, tw);
+  store_mixed2<N>(d, a, bm, kx);
 }
 
-// Restart from the compact state in W (a checkpoint): Y = W and the four
-// inverse column transforms of stage 1.  grid (Kc, B).
+// Restart from the compact state in W (a checkpoint): Y = W and the inverse
+// column transforms of u and v of stage 1.  grid (Kc, B).
 template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_state_cols(Dev d) {
   using G = Geo<N>;
@@ -352,7 +403,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_state_cols(Dev d) {
   double2 *tw = sm, *a = tw + N;
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
-  zero_outside<N>(a, 4);
+  zero_outside<N>(a, 2);
   #pragma unroll
   for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
     const int ky = ky_of_row(rr, G::K);
@@ -362,15 +413,17 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_state_cols(Dev d) {
     put_stage_columns<N>(a, kx, ky, w);
   }
   __syncthreads();
-  fft_batch<N, +1, 4>(a, tw);
-  store_mixed4<N>(d, a, bm, kx);
+  fft_batch<N, +1, 2>(a, tw);
+  store_mixed2<N>(d, a, bm, kx);
 }
 
 // ---------------------------------------------------------------------------
 // Forward RK stage
 // ---------------------------------------------------------------------------
 
-// Row pass of stage `stage` (1..4) of step n.  grid (N/2, B).
+// Row pass of stage `stage` (1..4) of step n: u, v of rows y0, y0+1; the
+// stage-field store and probe gather; the products u v and v^2 - u^2 and
+// their forward transforms along x into Mn.  grid (N/2, B).
 template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_rows(Dev d, int n, int stage, int flags) {
   using G = Geo<N>;
@@ -378,35 +431,27 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_rows(Dev d, int n, int 
   double2 *tw = sm, *a = tw + N;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
   load_twiddles<N>(tw, d.tw);
-  const double2* M = d.Mx + (size_t)bm * 4 * N * G::Kc;
-  // sequence 2*rr + g packs row y0+rr of fields (2g, 2g+1): (u, v) or (w_x, w_y)
-#pragma unroll
-  for (int seq = 0; seq < 4; ++seq) {
-    const int rr = seq >> 1, g = seq & 1;
-    pack_rows<N, G::THREADS>(a + seq * N, M + ((size_t)(2 * g) * N + y0 + rr) * G::Kc,
-                             M + ((size_t)(2 * g + 1) * N + y0 + rr) * G::Kc);
-  }
+  pack_field_pairs<N>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
   __syncthreads();
-  fft_batch<N, +1, 4>(a, tw);
+  fft_batch<N, +1, 2>(a, tw);
   const int st = N / d.px;
   const int slot = (flags & (F_OBS | F_OBS_ONLY)) ? obs_slot(d, n) : -1;
   double* trj = (flags & F_STORE)
-                    ? d.traj + (((size_t)bm * d.traj_steps + (n - d.seg0)) * 4 + (stage - 1)) * 4 * (size_t)N * N
+                    ? d.traj + (((size_t)bm * d.traj_steps + (n - d.seg0)) * 4 + (stage - 1)) * 2 * (size_t)N * N
                     : nullptr;
-  // one thread per column x handles both rows, then overwrites a[x] only
+  // one thread per column x reads (u, v) of both rows, then overwrites
+  // a[x] and a[N + x] only
   #pragma unroll
   for (int x = threadIdx.x; x < N; x += G::THREADS) {
-    double nl[2];
+    double pr[2], qr[2];
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
       const int y = y0 + rr;
-      const double2 uv = a[(2 * rr) * N + x], wg = a[(2 * rr + 1) * N + x];
+      const double2 uv = a[rr * N + x];
       if (trj) {
         const size_t o = (size_t)y * N + x;
         trj[o] = uv.x;
         trj[(size_t)N * N + o] = uv.y;
-        trj[(size_t)2 * N * N + o] = wg.x;
-        trj[(size_t)3 * N * N + o] = wg.y;
       }
       if (slot >= 0 && (y % st) == 0 && (x % st) == 0) {
         const int p = (y / st) * d.px + x / st;
@@ -414,26 +459,23 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_rows(Dev d, int n, int 
         o[0] = uv.x;
         o[1] = uv.y;
       }
-      nl[rr] = fma(uv.x, wg.x, uv.y * wg.y);
+      pr[rr] = uv.x * uv.y;
+      qr[rr] = fma(uv.y, uv.y, -uv.x * uv.x);
     }
-    a[x] = make_double2(nl[0], nl[1]);
+    a[x] = make_double2(pr[0], pr[1]);
+    a[N + x] = make_double2(qr[0], qr[1]);
   }
   if (flags & F_OBS_ONLY) return;
   __syncthreads();
-  fft_batch<N, -1, 1>(a, tw);
-  double2* O = d.Mn + ((size_t)bm * N + y0) * G::Kc;
-  #pragma unroll
-  for (int kx = threadIdx.x; kx < G::Kc; kx += G::THREADS) {
-    double2 A, Bv;
-    unpack_pair<N>(a, kx, A, Bv);
-    O[kx] = A;
-    O[G::Kc + kx] = Bv;
-  }
+  fft_batch<N, -1, 2>(a, tw);
+  unpack_field_rows<N>(a, d.Mn + (size_t)bm * 2 * N * G::Kc, y0);
 }
 
-// Column pass of stage `stage`: k_j = -P DFT(u.grad w) - nu k^2 y_j + f_hat,
-// the RK4 update, and the inverse column transforms of the next stage
-// state.  Acc holds k1 + 2 k2 + 2 k3 (+ k4).  grid (Kc, B).
+// Column pass of stage `stage`: the advection term
+//   n_hat = (ky^2 - kx^2) DFT(u v) - kx ky DFT(v^2 - u^2),
+// k_j = -n_hat - nu k^2 y_j + f_hat, the RK4 update, and the inverse column
+// transforms of u and v of the next stage state.  Acc holds k1 + 2 k2 +
+// 2 k3 (+ k4).  grid (Kc, B).
 template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, int flags) {
   using G = Geo<N>;
@@ -441,18 +483,21 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, 
   double2 *tw = sm, *a = tw + N;
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
-  const double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
-  load_column<N, G::THREADS, 1>(a, M);
+  load_column<N, G::THREADS, 2>(a, d.Mn + (size_t)bm * 2 * N * G::Kc + kx);
   __syncthreads();
-  fft_batch<N, -1, 1>(a, tw);
+  fft_batch<N, -1, 2>(a, tw);
   const double dt = d.dt;
   const double fval = -d.amp * d.nf * (double)N * N / 2.0;
-  // each retained position is read and rewritten by one thread only
+  // each retained position is read and rewritten (both sequences) by one
+  // thread only
   #pragma unroll
   for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
     const int ky = ky_of_row(rr, G::K);
+    const int qi = ky & (N - 1);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
-    const double2 nh = a[ky & (N - 1)];
+    const double2 ph = a[qi], qh = a[N + qi];
+    const double cp = (double)(ky * ky - kx * kx), cq = -(double)(kx * ky);
+    const double2 nh = make_double2(fma(cp, ph.x, cq * qh.x), fma(cp, ph.y, cq * qh.y));
     const double2 yv = d.Y[idx];
     const double k2 = (double)(kx * kx + ky * ky);
     double2 F = make_double2(-nh.x - d.nu * k2 * yv.x, -nh.y - d.nu * k2 * yv.y);
@@ -480,10 +525,10 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, 
     put_stage_columns<N>(a, kx, ky, ynext);
   }
   if (flags & F_NO_NEXT) return;
-  zero_outside<N>(a, 4);
+  zero_outside<N>(a, 2);
   __syncthreads();
-  fft_batch<N, +1, 4>(a, tw);
-  store_mixed4<N>(d, a, bm, kx);
+  fft_batch<N, +1, 2>(a, tw);
+  store_mixed2<N>(d, a, bm, kx);
 }
 
 // r = model observations - data and J = 1/2 sum r^2 per member, in a fixed
@@ -508,6 +553,14 @@ __global__ void k_sobolev_grad(double2* lam, const double2* w0, double lambda, i
 // ---------------------------------------------------------------------------
 // Adjoint
 // ---------------------------------------------------------------------------
+//
+// The tangent of the advection term at (u, v) is
+//   dn = (d_xx - d_yy)(u dv + v du) + d_xy (2 v dv - 2 u du),
+// so its transpose applied to kbar is, with a = IDFT(d_xy kbar) and
+// b = IDFT((d_xx - d_yy) kbar) on the grid,
+//   rho_u = v b - 2 u a,   rho_v = u b + 2 v a,
+//   J^T kbar = -P[(-i ky/k^2) DFT(rho_u) + (i kx/k^2) DFT(rho_v)] - nu k^2 kbar,
+// the transposes of du = IDFT(i ky/k^2 dw), dv = IDFT(-i kx/k^2 dw).
 
 // Separable DFT of the residual at observation slot `slot` on the probe
 // lattice: for each lattice row, T(kx) = sum_q r[row][q] W_P^{kx q}; the
@@ -547,41 +600,46 @@ __device__ __forceinline__ double2 probe_source(const Dev& d, int kx, int ky, co
 }
 
 // Start of the adjoint sweep: LamBar = (terminal field in LamBar, with
-// INIT_LAMBAR) + (H^T r at the last step, with INIT_SRC), KB = dt/6 LamBar
-// and its inverse column transform into Mn.  grid (Kc, B).
+// INIT_LAMBAR) + (H^T r at the last step, with INIT_SRC), KB = dt/6 LamBar;
+// with INIT_RESUME, KB as it stands (after a checkpoint recompute).  Then
+// the inverse column transforms of the adjoint fields a, b of KB into Mx.
+// grid (Kc, B).
 template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_init(Dev d, int mode) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *Tu = a + 4 * N, *Tv = Tu + G::PMAX;
+  double2 *tw = sm, *a = tw + N, *Tu = a + 2 * N, *Tv = Tu + G::PMAX;
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
-  const int slot = (mode & INIT_SRC) ? obs_slot(d, d.nsteps) : -1;
+  const bool resume = (mode & INIT_RESUME) != 0;
+  const int slot = (!resume && (mode & INIT_SRC)) ? obs_slot(d, d.nsteps) : -1;
   if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
-  zero_outside<N>(a, 1);
+  zero_outside<N>(a, 2);
   __syncthreads();
-  const double s = 1.0 / ((double)N * N);
   #pragma unroll
   for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
     const int ky = ky_of_row(rr, G::K);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
-    double2 lam = (mode & INIT_LAMBAR) ? d.LamBar[idx] : make_double2(0.0, 0.0);
-    if (slot >= 0) lam = cadd(lam, probe_source(d, kx, ky, Tu, Tv));
-    d.LamBar[idx] = lam;
-    const double2 kb = cscale(lam, d.dt / 6.0);
-    d.KB[idx] = kb;
-    a[ky & (N - 1)] = cscale(kb, s);
+    double2 kb;
+    if (resume) {
+      kb = d.KB[idx];
+    } else {
+      double2 lam = (mode & INIT_LAMBAR) ? d.LamBar[idx] : make_double2(0.0, 0.0);
+      if (slot >= 0) lam = cadd(lam, probe_source(d, kx, ky, Tu, Tv));
+      d.LamBar[idx] = lam;
+      kb = cscale(lam, d.dt / 6.0);
+      d.KB[idx] = kb;
+    }
+    put_adjoint_columns<N>(a, kx, ky, kb);
   }
   __syncthreads();
-  fft_batch<N, +1, 1>(a, tw);
-  double2* M = d.Mn + (size_t)bm * N * G::Kc + kx;
-  #pragma unroll
-  for (int y = threadIdx.x; y < N; y += G::THREADS) M[(size_t)y * G::Kc] = a[y];
+  fft_batch<N, +1, 2>(a, tw);
+  store_mixed2<N>(d, a, bm, kx);
 }
 
-// Adjoint row pass of stage `stage` of step n: mu = inverse transform along x
-// of the mixed kbar rows (two rows packed), products with the stored u, v,
-// w_x, w_y, and their forward transforms along x.  grid (N/2, B).
+// Adjoint row pass of stage `stage` of step n: a, b of rows y0, y0+1
+// (inverse transforms along x), rho_u and rho_v with the stored u, v, and
+// their forward transforms along x into Mn.  grid (N/2, B).
 template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_rows(Dev d, int n, int stage) {
   using G = Geo<N>;
@@ -589,81 +647,66 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_rows(Dev d, int n, int 
   double2 *tw = sm, *a = tw + N;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
   load_twiddles<N>(tw, d.tw);
-  const double2* M = d.Mn + ((size_t)bm * N + y0) * G::Kc;
-  pack_rows<N, G::THREADS>(a, M, M + G::Kc);
+  pack_field_pairs<N>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
   __syncthreads();
-  fft_batch<N, +1, 1>(a, tw);
-  const double* trj = d.traj + (((size_t)bm * d.traj_steps + (n - d.seg0)) * 4 + (stage - 1)) * 4 * (size_t)N * N;
-  // one thread per column x reads a[x] (mu of both rows), then writes the
-  // four product sequences at x
+  fft_batch<N, +1, 2>(a, tw);
+  const double* trj = d.traj + (((size_t)bm * d.traj_steps + (n - d.seg0)) * 4 + (stage - 1)) * 2 * (size_t)N * N;
+  // one thread per column x reads (a, b) of both rows, then writes
+  // rho_u and rho_v of both rows at x
   #pragma unroll
   for (int x = threadIdx.x; x < N; x += G::THREADS) {
-    const double2 mu = a[x];
+    double ru[2], rv[2];
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
-      const double m = rr ? mu.y : mu.x;
+      const double2 ab = a[rr * N + x];
       const size_t o = (size_t)(y0 + rr) * N + x;
       const double fu = trj[o], fv = trj[(size_t)N * N + o];
-      const double fwx = trj[(size_t)2 * N * N + o], fwy = trj[(size_t)3 * N * N + o];
-      a[(2 * rr) * N + x] = make_double2(fu * m, fv * m);
-      a[(2 * rr + 1) * N + x] = make_double2(fwx * m, fwy * m);
+      ru[rr] = fma(fv, ab.y, -2.0 * fu * ab.x);
+      rv[rr] = fma(fu, ab.y, 2.0 * fv * ab.x);
     }
+    a[x] = make_double2(ru[0], ru[1]);
+    a[N + x] = make_double2(rv[0], rv[1]);
   }
   __syncthreads();
-  fft_batch<N, -1, 4>(a, tw);
-  double2* O = d.Mx + (size_t)bm * 4 * N * G::Kc;
-  #pragma unroll
-  for (int u = threadIdx.x; u < 4 * G::Kc; u += G::THREADS) {
-    const int seq = u / G::Kc, kx = u - seq * G::Kc;
-    const int rr = seq >> 1, g = seq & 1;
-    double2 A, Bv;
-    unpack_pair<N>(a + seq * N, kx, A, Bv);
-    O[((size_t)(2 * g) * N + y0 + rr) * G::Kc + kx] = A;
-    O[((size_t)(2 * g + 1) * N + y0 + rr) * G::Kc + kx] = Bv;
-  }
+  fft_batch<N, -1, 2>(a, tw);
+  unpack_field_rows<N>(a, d.Mn + (size_t)bm * 2 * N * G::Kc, y0);
 }
 
 // Adjoint column pass of stage `stage` of step n:
-//   ybar_j = P[ i ky/k^2 D(w_x mu) - i kx/k^2 D(w_y mu) + i kx D(u mu)
-//              + i ky D(v mu) ] - nu k^2 kbar_j,
+//   ybar_j = -P[(-i ky/k^2) DFT(rho_u) + (i kx/k^2) DFT(rho_v)] - nu k^2 kbar_j,
 // the transposed RK4 combination, the observation source at step n (on
-// stage 1), and the inverse column transform of the next kbar.
+// stage 1), and the inverse column transforms of a, b of the next kbar.
 // grid (Kc, B).
 template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int stage, int flags) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *Tu = a + 4 * N, *Tv = Tu + G::PMAX;
+  double2 *tw = sm, *a = tw + N, *Tu = a + 2 * N, *Tv = Tu + G::PMAX;
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_twiddles<N>(tw, d.tw);
-  const double2* M = d.Mx + (size_t)bm * 4 * N * G::Kc + kx;
-  load_column<N, G::THREADS, 4>(a, M);
+  load_column<N, G::THREADS, 2>(a, d.Mn + (size_t)bm * 2 * N * G::Kc + kx);
   const int slot = (flags & F_SRC) ? obs_slot(d, n) : -1;
   if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
   __syncthreads();
-  fft_batch<N, -1, 4>(a, tw);
+  fft_batch<N, -1, 2>(a, tw);
   const double dt = d.dt;
-  const double s = 1.0 / ((double)N * N);
-  // each retained position is read (four sequences) and rewritten (first
-  // sequence) by one thread only
+  // each retained position is read and rewritten (both sequences) by one
+  // thread only
   #pragma unroll
   for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
     const int ky = ky_of_row(rr, G::K);
     const int qi = ky & (N - 1);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
-    const double2 P1 = a[qi], P2 = a[N + qi], P3 = a[2 * N + qi], P4 = a[3 * N + qi];
+    const double2 Ru = a[qi], Rv = a[N + qi];
     const double k2 = (double)(kx * kx + ky * ky);
     const double ik2 = k2 > 0.0 ? 1.0 / k2 : 0.0;
     const double a1 = ky * ik2, c1 = kx * ik2;
-    // terms of the transposed products (conjugate symbols), subtracted in turn
-    const double2 t0 = make_double2(a1 * P3.y, -a1 * P3.x);   // (-i ky/k^2) D(w_x mu)
-    const double2 t1 = make_double2(-c1 * P4.y, c1 * P4.x);   // ( i kx/k^2) D(w_y mu)
-    const double2 t2 = make_double2(kx * P1.y, -kx * P1.x);   // (-i kx) D(u mu)
-    const double2 t3 = make_double2(ky * P2.y, -ky * P2.x);   // (-i ky) D(v mu)
+    // t = (-i ky/k^2) Ru + (i kx/k^2) Rv
+    const double2 t = make_double2(fma(a1, Ru.y, -c1 * Rv.y), fma(-a1, Ru.x, c1 * Rv.x));
     const double2 kb = d.KB[idx];
     double2 yb;
-    yb.x = (((-t0.x) - t1.x) - t2.x) - t3.x - d.nu * k2 * kb.x;
-    yb.y = (((-t0.y) - t1.y) - t2.y) - t3.y - d.nu * k2 * kb.y;
+    yb.x = -t.x - d.nu * k2 * kb.x;
+    yb.y = -t.y - d.nu * k2 * kb.y;
     const double2 lb = d.LamBar[idx];
     double2 nk;
     if (stage == 4) {
@@ -685,15 +728,13 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int 
       nk = cscale(lam, dt / 6.0);
     }
     d.KB[idx] = nk;
-    a[qi] = cscale(nk, s);
+    put_adjoint_columns<N>(a, kx, ky, nk);
   }
   if (flags & F_FINAL) return;
-  zero_outside<N>(a, 1);
+  zero_outside<N>(a, 2);
   __syncthreads();
-  fft_batch<N, +1, 1>(a, tw);
-  double2* O = d.Mn + (size_t)bm * N * G::Kc + kx;
-  #pragma unroll
-  for (int y = threadIdx.x; y < N; y += G::THREADS) O[(size_t)y * G::Kc] = a[y];
+  fft_batch<N, +1, 2>(a, tw);
+  store_mixed2<N>(d, a, bm, kx);
 }
 
 // Control multipliers m(k) = |k| W(k)^{1/2} on the retained set (0 at k = 0),

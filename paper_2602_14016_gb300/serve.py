@@ -68,13 +68,13 @@ def context_bytes(n: int, nsteps: int, px: int, every: int, ckpt_every: int, bat
     Kc, Kr = K + 1, 2 * K + 1
     nt = nsteps // every
     comp = batch * Kr * Kc * 16
-    b = 6 * comp + batch * 5 * n * Kc * 16 + 3 * batch * nt * px * px * 2 * 8 + comp // 2
+    b = 6 * comp + batch * 4 * n * Kc * 16 + 3 * batch * nt * px * px * 2 * 8 + comp // 2
     b += n * 16 + px * 16 + batch * (8 + 4 + 8) + batch * 8
     if ckpt_every == 0:
-        b += batch * nsteps * 16 * n * n * 8
+        b += batch * nsteps * 8 * n * n * 8
     else:
         kk = min(ckpt_every, nsteps)
-        b += batch * kk * 16 * n * n * 8 + ((nsteps + kk - 1) // kk) * comp
+        b += batch * kk * 8 * n * n * 8 + ((nsteps + kk - 1) // kk) * comp
     slots = memory + 1
     b += batch * (5 + 2 * slots) * n * n * 8 + batch * (((n * n + 8191) // 8192) + 3) * 8 + 2 * batch * 8
     return int(b)

@@ -154,7 +154,7 @@ def autograd_check(api, torch, n=512, nsteps=4000, dt=1e-3, nu=1 / 200, nf=4, ck
         floors.append(4 * np.finfo(float).eps * abs(Lval) / (2 * eps) / max(abs(gd), 1e-300))
     errs, floors = np.array(errs), np.array(floors)
     out = {"n": n, "nsteps": nsteps, "ckpt_every": ckpt_every, "device_bytes": ctx.device_bytes,
-           "full_storage_bytes": nsteps * 16 * n * n * 8, "loss": Lval, "grad_seconds": t_grad,
+           "full_storage_bytes": nsteps * 8 * n * n * 8, "loss": Lval, "grad_seconds": t_grad,
            "fd_rel_err_max": float(errs.max()), "fd_rel_err_median": float(np.median(errs)),
            "fd_rounding_floor_median": float(np.median(floors)),
            "directions_within_10x_floor_or_1e-6": int(np.sum(errs <= np.maximum(10 * floors, 1e-6))),
