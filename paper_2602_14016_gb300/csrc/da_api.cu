@@ -196,6 +196,9 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
   d.px = c->P;
   d.nt = c->nt;
   d.dt = c->dt;
+  d.dt2 = c->dt / 2.0;
+  d.dt3 = c->dt / 3.0;
+  d.dt6 = c->dt / 6.0;
   d.nu = nu;
   d.force = f.kind == DA_FORCE_KOLMOGOROV;
   d.amp = f.amp;
@@ -219,8 +222,11 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
   A(dalloc(c, &d.res, B * c->nt * P2 * 2));
   A(dalloc(c, &d.J, B));
   A(dalloc(c, (double**)&d.mult, comp));
-  A(dalloc(c, (double2**)&d.tw, N));
+  A(dalloc(c, (double**)&d.fold, (size_t)ops->fold_doubles));
   A(dalloc(c, (double2**)&d.twP, (size_t)c->P));
+  A(dalloc(c, (da::Sym4**)&d.symF, comp / B));
+  A(dalloc(c, (da::Sym4**)&d.symA, comp / B));
+  A(dalloc(c, (double**)&d.nuk2, comp / B));
   // stage-field store: the whole window, or one checkpoint segment
   if (c->ckpt == 0) {
     d.traj_steps = c->nsteps;
@@ -242,16 +248,37 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
     da_destroy(c);
     return s;
   }
-  // constant tables: twiddles of the FFT plan and of the probe lattice
-  std::vector<double2> tw = roots_of_unity(n), twP = roots_of_unity(c->P);
+  // constant tables: folded twiddles of the FFT plan, twiddles of the probe
+  // lattice
+  std::vector<double> fold(ops->fold_doubles);
+  ops->fold_table(fold.data());
+  std::vector<double2> twP = roots_of_unity(c->P);
   std::vector<int> kind(B);
   std::vector<double> param(B);
   for (size_t b = 0; b < B; ++b) {
     kind[b] = kernels[b].kind;
     param[b] = kernels[b].param;
   }
-  cudaError_t e = cudaMemcpy((void*)d.tw, tw.data(), N * sizeof(double2), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMemcpy((void*)d.fold, fold.data(), fold.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy((void*)d.twP, twP.data(), c->P * sizeof(double2), cudaMemcpyHostToDevice);
+  // per-mode symbols of the column passes, column-major [Kc][Kr]
+  const int K = ops->K, Kr = ops->Kr, Kc = ops->Kc;
+  std::vector<da::Sym4> symF((size_t)Kr * Kc), symA((size_t)Kr * Kc);
+  std::vector<double> nuk2((size_t)Kr * Kc);
+  const double s2 = 1.0 / ((double)n * n);
+  for (int kx = 0; kx < Kc; ++kx)
+    for (int r = 0; r < Kr; ++r) {
+      const int ky = r <= K ? r : r - Kr;
+      const double k2 = (double)(kx * kx + ky * ky);
+      const double ik2 = k2 > 0.0 ? 1.0 / k2 : 0.0;
+      const size_t i = (size_t)kx * Kr + r;
+      symF[i] = {ky * ik2 * s2, kx * ik2 * s2, 0.5 * (ky * ky - kx * kx), -0.5 * kx * ky};
+      symA[i] = {0.5 * ky * ik2, 0.5 * kx * ik2, -2.0 * kx * ky * s2, (double)(ky * ky - kx * kx) * s2};
+      nuk2[i] = nu * k2;
+    }
+  if (e == cudaSuccess) e = cudaMemcpy((void*)d.symF, symF.data(), symF.size() * sizeof(da::Sym4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy((void*)d.symA, symA.data(), symA.size() * sizeof(da::Sym4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy((void*)d.nuk2, nuk2.data(), nuk2.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_kind, kind.data(), B * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_param, param.data(), B * sizeof(double), cudaMemcpyHostToDevice);
   for (size_t b = 0; b < B && e == cudaSuccess; ++b)

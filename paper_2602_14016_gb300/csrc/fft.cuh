@@ -18,6 +18,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 namespace da {
 
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -206,6 +208,196 @@ template <int N, int S, int F, int L, int R, int... Rs>
 __device__ __forceinline__ void run_stages(double2* buf, const double2* tw, Radices<R, Rs...>) {
   stockham_stage<N, R, S, F>(buf, L, tw);
   run_stages<N, S, F, L * R>(buf, tw, Radices<Rs...>{});
+}
+
+// ---------------------------------------------------------------------------
+// Folded twiddles
+// ---------------------------------------------------------------------------
+//
+// A twiddle w = exp(S i theta) written as c (1 + i t), c = cos theta,
+// t = S tan theta, turns w a into c z with z = (a.x - t a.y, a.y + t a.x):
+// two FMAs.  The factor c then rides on the FMAs of the butterfly that
+// follows: in a radix-4 butterfly, a0 +- c2 z2 and, with r31 = c3/c1,
+// c1 (z1 +- r31 z3); in a radix-8 butterfly the even half is a folded
+// radix-4 on (a0, a2, a4, a6) and every output of the odd half carries the
+// common factor c1, which joins the last combination (for k = 1, 3 as
+// kR2 c1).  A twiddled radix-4 butterfly costs 22 FP64 instructions instead
+// of 28 and a twiddled radix-8 one 66 instead of 80.  c is never exactly
+// zero (the angles are below pi/2 for c1, and elsewhere cos of a rounded
+// angle), and c t, c r reconstitute sin theta and the other cosines to a
+// rounding, so every output keeps an error of a few ulps of the inputs.
+//
+// Per stage with L > 1 the table holds, slot-major (slot j of butterfly
+// class k at j * L + k):
+//   R = 4: t1 t2 t3 (for S = -1), c1, c2, r31;
+//   R = 8: t1..t7, c1, c2, c4, r62 = c6/c2, r51 = c5/c1, r73 = c7/c3,
+//          r31 = c3/c1, q = cos(pi/4) c1.
+
+template <int R> struct FoldSlots { static constexpr int value = 0; };  // untwiddled first stages only
+template <> struct FoldSlots<4> { static constexpr int value = 6; };
+template <> struct FoldSlots<8> { static constexpr int value = 15; };
+
+// Doubles of the folded table of a plan, stages after the first.
+template <int L, typename P> struct FoldSize;
+template <int L> struct FoldSize<L, Radices<>> { static constexpr int value = 0; };
+template <int L, int R, int... Rs> struct FoldSize<L, Radices<R, Rs...>> {
+  static constexpr int value = (L > 1 ? FoldSlots<R>::value * L : 0) + FoldSize<L * R, Radices<Rs...>>::value;
+};
+
+template <int N>
+struct FoldInfo {
+  static constexpr int DOUBLES = FoldSize<1, typename Plan<N>::two>::value;
+  // padded to whole double2 so that the sequences after it stay aligned
+  static constexpr int PADDED = (DOUBLES + 1) / 2 * 2;
+};
+
+// z = (a.x - t a.y, a.y + t a.x)
+__device__ __forceinline__ double2 tan_rot(double2 a, double t) {
+  return make_double2(fma(-t, a.y, a.x), fma(t, a.x, a.y));
+}
+
+// e +- c z  (plus, minus)
+__device__ __forceinline__ void fma_pair(double2 e, double2 z, double c, double2& plus, double2& minus) {
+  plus = make_double2(fma(c, z.x, e.x), fma(c, z.y, e.y));
+  minus = make_double2(fma(-c, z.x, e.x), fma(-c, z.y, e.y));
+}
+
+// Twiddled radix-4 butterfly with folded twiddles (table T, class k, L).
+template <int S>
+__device__ __forceinline__ void dft4_folded(double2* a, const double* T, int k, int L) {
+  const double sg = S < 0 ? 1.0 : -1.0;
+  const double t1 = sg * T[k], t2 = sg * T[L + k], t3 = sg * T[2 * L + k];
+  const double c1 = T[3 * L + k], c2 = T[4 * L + k], r31 = T[5 * L + k];
+  const double2 z1 = tan_rot(a[1], t1), z2 = tan_rot(a[2], t2), z3 = tan_rot(a[3], t3);
+  double2 t0, tt1, u, v;
+  fma_pair(a[0], z2, c2, t0, tt1);
+  fma_pair(z1, z3, r31, u, v);
+  fma_pair(t0, u, c1, a[0], a[2]);
+  fma_pair(tt1, mul_si<S>(v), c1, a[1], a[3]);
+}
+
+// Twiddled radix-8 butterfly with folded twiddles.
+template <int S>
+__device__ __forceinline__ void dft8_folded(double2* a, const double* T, int k, int L) {
+  const double sg = S < 0 ? 1.0 : -1.0;
+  double2 z[8];
+#pragma unroll
+  for (int m = 1; m < 8; ++m) z[m] = tan_rot(a[m], sg * T[(m - 1) * L + k]);
+  const double c1 = T[7 * L + k], c2 = T[8 * L + k], c4 = T[9 * L + k];
+  const double r62 = T[10 * L + k], r51 = T[11 * L + k], r73 = T[12 * L + k], r31 = T[13 * L + k];
+  const double q = T[14 * L + k];
+  // even half: radix 4 on (a0, a2', a4', a6')
+  double2 et0, et1, eu, ev, e0, e1, e2, e3;
+  fma_pair(a[0], z[4], c4, et0, et1);
+  fma_pair(z[2], z[6], r62, eu, ev);
+  fma_pair(et0, eu, c2, e0, e2);
+  fma_pair(et1, mul_si<S>(ev), c2, e1, e3);
+  // odd half on (a1', a3', a5', a7'), outputs c1 p_k
+  double2 ou0, ov0, ou1, ov1, p0, p1, p2, p3;
+  fma_pair(z[1], z[5], r51, ou0, ov0);
+  fma_pair(z[3], z[7], r73, ou1, ov1);
+  fma_pair(ou0, ou1, r31, p0, p2);
+  fma_pair(ov0, mul_si<S>(ov1), r31, p1, p3);
+  // a_k = e_k + W8^k c1 p_k
+  fma_pair(e0, p0, c1, a[0], a[4]);
+  fma_pair(e2, mul_si<S>(p2), c1, a[2], a[6]);
+  const double2 w1 = make_double2(p1.x - S * p1.y, p1.y + S * p1.x);
+  fma_pair(e1, w1, q, a[1], a[5]);
+  const double2 w3 = make_double2(p3.x + S * p3.y, p3.y - S * p3.x);
+  fma_pair(e3, w3, -q, a[3], a[7]);
+}
+
+// One in-place Stockham stage with folded twiddles (T: this stage's table).
+template <int N, int R, int S, int F, int L>
+__device__ __forceinline__ void stockham_stage_folded(double2* buf, const double* __restrict__ T) {
+  constexpr int NB = N / R, Th = PlanInfo<N>::THREADS, TOT = F * NB, J = (TOT + Th - 1) / Th;
+  double2 a[J][R];
+  int base[J], dst[J];
+#pragma unroll
+  for (int jb = 0; jb < J; ++jb) {
+    const int u = threadIdx.x + jb * Th;
+    base[jb] = 0;
+    dst[jb] = 0;
+    if (TOT % Th == 0 || u < TOT) {
+      const int f = u / NB;
+      const int i = u - f * NB;
+      const int k = i & (L - 1);
+      base[jb] = f * N;
+#pragma unroll
+      for (int m = 0; m < R; ++m) a[jb][m] = buf[base[jb] + i + m * NB];
+      if constexpr (L == 1) {
+        dftR<R, S>(a[jb]);
+      } else {
+        static_assert(R == 4 || R == 8, "folded twiddles for radix 4 and 8");
+        if constexpr (R == 4) dft4_folded<S>(a[jb], T, k, L);
+        if constexpr (R == 8) dft8_folded<S>(a[jb], T, k, L);
+      }
+      dst[jb] = (i - k) * R + k;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int jb = 0; jb < J; ++jb) {
+    const int u = threadIdx.x + jb * Th;
+    if (TOT % Th == 0 || u < TOT) {
+#pragma unroll
+      for (int m = 0; m < R; ++m) buf[base[jb] + dst[jb] + m * L] = a[jb][m];
+    }
+  }
+  __syncthreads();
+}
+
+template <int N, int S, int F, int L>
+__device__ __forceinline__ void run_stages_folded(double2*, const double*, Radices<>) {}
+
+template <int N, int S, int F, int L, int R, int... Rs>
+__device__ __forceinline__ void run_stages_folded(double2* buf, const double* T, Radices<R, Rs...>) {
+  stockham_stage_folded<N, R, S, F, L>(buf, T);
+  run_stages_folded<N, S, F, L * R>(buf, T + (L > 1 ? FoldSlots<R>::value * L : 0), Radices<Rs...>{});
+}
+
+// Transform, in place, F (1 or 2) sequences of N points stored back to back
+// in buf, with the folded table of Plan<N>::two (both plans of a size are
+// the same list of radices) in shared memory.  Same contract as fft_batch.
+template <int N, int S, int F>
+__device__ __forceinline__ void fft_folded(double2* buf, const double* T) {
+  static_assert(F == 1 || F == 2, "batches of one or two transforms");
+  run_stages_folded<N, S, F, 1>(buf, T, typename Plan<N>::two{});
+}
+
+// Host side: fill the folded table of Plan<N>::two (FoldInfo<N>::DOUBLES
+// entries) for S = -1.
+template <int L>
+inline void fold_fill(double*, int, Radices<>) {}
+
+template <int L, int R, int... Rs>
+inline void fold_fill(double* out, int n, Radices<R, Rs...>) {
+  if (L > 1) {
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < L; ++k) {
+      double c[8], t[8];
+      for (int m = 1; m < R; ++m) {
+        const double th = -2.0 * pi * (double)(m * k) / (double)(L * R);  // W_{LR}^{mk}, S = -1
+        c[m] = std::cos(th);
+        t[m] = std::tan(th);
+      }
+      if (R == 4) {
+        const double v[6] = {t[1], t[2], t[3], c[1], c[2], c[3] / c[1]};
+        for (int j = 0; j < 6; ++j) out[j * L + k] = v[j];
+      } else {
+        const double v[15] = {t[1], t[2], t[3], t[4], t[5], t[6], t[7], c[1], c[2], c[4],
+                              c[6] / c[2], c[5] / c[1], c[7] / c[3], c[3] / c[1], 0.70710678118654752440 * c[1]};
+        for (int j = 0; j < 15; ++j) out[j * L + k] = v[j];
+      }
+    }
+    out += FoldSlots<R>::value * L;
+  }
+  fold_fill<L * R>(out, n, Radices<Rs...>{});
+}
+
+template <int N>
+inline void fold_table(double* out) {
+  fold_fill<1>(out, N, typename Plan<N>::two{});
 }
 
 // Transform, in place, F (1 or 2) sequences of N points stored back to back

@@ -53,6 +53,20 @@ enum : int { INIT_SRC = 1, INIT_LAMBAR = 2, INIT_RESUME = 4 };
 // Multipliers of the generic spectral-to-mixed column pass.
 enum : int { M_ONE = 0, M_CTRL = 1, M_FILTERED = 2, M_INV_CTRL = 3 };
 
+// Per-mode constants of the column passes, column-major [Kc][Kr] (entry
+// kx * Kr + r), computed once on the host so that no column pass divides or
+// converts integers in FP64:
+//   fwd: su = ky/k^2/N^2, sv = kx/k^2/N^2 (u, v columns of a state value),
+//        cp = (ky^2 - kx^2)/2, cq = -kx ky/2 (advection symbols; the 1/2 is
+//        the one the row pass leaves out when it unpacks two real rows);
+//   adj: a1 = ky/k^2/2, c1 = kx/k^2/2 (transposed velocity symbols, same
+//        1/2), ca = -2 kx ky/N^2, cb = (ky^2 - kx^2)/N^2 (adjoint-field
+//        columns; ca carries the 2 of rho_u, rho_v);
+//   nuk2 = nu k^2.
+struct __align__(32) Sym4 {
+  double a, b, c, d;
+};
+
 // Everything a kernel needs, passed by value.
 struct Dev {
   int B, nsteps, every, include_t0, px, nt;
@@ -71,8 +85,12 @@ struct Dev {
   double* res;                               // residuals [B][nt][P2][2]
   double* J;                                 // [B]
   const double* mult;                        // control multiplier |k| W^1/2, [B][Kr][Kc]
-  const double2* tw;                         // W_N^t, t < N
+  const double* fold;                        // folded twiddles of Plan<N> (fft.cuh)
   const double2* twP;                        // W_P^t, t < P
+  const Sym4* symF;                          // [Kc][Kr] su, sv, cp, cq
+  const Sym4* symA;                          // [Kc][Kr] a1, c1, ca, cb
+  const double* nuk2;                        // [Kc][Kr] nu k^2
+  double dt2, dt3, dt6;                      // dt/2, dt/3, dt/6
 };
 
 template <int N>
@@ -83,16 +101,17 @@ struct Geo {
   static constexpr int NH = N / 2 + 1;
   // threads: two transforms at a time (fft.cuh)
   static constexpr int THREADS = PlanInfo<N>::THREADS;
-  // shared memory: twiddles + one buffer of two sequences + probe sums
+  // shared memory: folded twiddle table + one buffer of two sequences +
+  // probe sums
   static constexpr int PMAX = 64;
-  static constexpr size_t SMEM = sizeof(double2) * (N + 2 * N + 2 * PMAX);
+  static constexpr size_t SMEM = sizeof(double) * FoldInfo<N>::PADDED + sizeof(double2) * (2 * N + 2 * PMAX);
 };
 
 __device__ __forceinline__ int ky_of_row(int r, int K) { return r <= K ? r : r - (2 * K + 1); }
 
 template <int N>
-__device__ __forceinline__ void load_twiddles(double2* tw, const double2* __restrict__ g) {
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g[i];
+__device__ __forceinline__ void load_fold(double* T, const double* __restrict__ g) {
+  for (int i = threadIdx.x; i < FoldInfo<N>::DOUBLES; i += blockDim.x) T[i] = g[i];
 }
 
 // Observation slot of step k, or -1.
@@ -157,6 +176,15 @@ __device__ __forceinline__ void unpack_pair(const double2* Z, int kx, double2& A
   Bv = make_double2(0.5 * ty, -0.5 * tx);
 }
 
+// Twice the two half spectra (no 1/2): the pass kernels fold the 1/2 into
+// the per-mode symbols of the column pass that consumes them.
+template <int N>
+__device__ __forceinline__ void unpack_pair2(const double2* Z, int kx, double2& A, double2& Bv) {
+  const double2 zk = Z[kx], zm = Z[(N - kx) & (N - 1)];
+  A = make_double2(zk.x + zm.x, zk.y - zm.y);
+  Bv = make_double2(zk.y + zm.y, zm.x - zk.x);
+}
+
 // ---------------------------------------------------------------------------
 // Generic row transforms (control map, gradient map)
 // ---------------------------------------------------------------------------
@@ -167,14 +195,15 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_r2c_rows(Dev d, const double* __restrict__ in) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N;
+  double* T = reinterpret_cast<double*>(sm);
+  double2* a = sm + FoldInfo<N>::PADDED / 2;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
-  load_twiddles<N>(tw, d.tw);
+  load_fold<N>(T, d.fold);
   const double* r0 = in + ((size_t)bm * N + y0) * N;
   #pragma unroll
   for (int x = threadIdx.x; x < N; x += G::THREADS) a[x] = make_double2(r0[x], r0[N + x]);
   __syncthreads();
-  fft_batch<N, -1, 1>(a, tw);
+  fft_folded<N, -1, 1>(a, T);
   double2* M = d.Mn + ((size_t)bm * 2 * N + y0) * G::Kc;
   #pragma unroll
   for (int kx = threadIdx.x; kx < G::Kc; kx += G::THREADS) {
@@ -191,13 +220,14 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_c2r_rows(Dev d, double* __restrict__ out) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N;
+  double* T = reinterpret_cast<double*>(sm);
+  double2* a = sm + FoldInfo<N>::PADDED / 2;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
-  load_twiddles<N>(tw, d.tw);
+  load_fold<N>(T, d.fold);
   const double2* M = d.Mn + ((size_t)bm * 2 * N + y0) * G::Kc;
   pack_rows<N, G::THREADS>(a, M, M + G::Kc);
   __syncthreads();
-  fft_batch<N, +1, 1>(a, tw);
+  fft_folded<N, +1, 1>(a, T);
   double* r0 = out + ((size_t)bm * N + y0) * N;
   #pragma unroll
   for (int x = threadIdx.x; x < N; x += G::THREADS) {
@@ -212,9 +242,10 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_spec_to_mixed(Dev d, const double2* __restrict__ src, int mode) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N;
+  double* T = reinterpret_cast<double*>(sm);
+  double2* a = sm + FoldInfo<N>::PADDED / 2;
   const int kx = blockIdx.x, bm = blockIdx.y;
-  load_twiddles<N>(tw, d.tw);
+  load_fold<N>(T, d.fold);
   const double s = 1.0 / ((double)N * N);
   #pragma unroll
   for (int q = threadIdx.x; q < N; q += G::THREADS) {
@@ -234,7 +265,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_spec_to_mixed(Dev d, const 
     a[q] = v;
   }
   __syncthreads();
-  fft_batch<N, +1, 1>(a, tw);
+  fft_folded<N, +1, 1>(a, T);
   double2* M = d.Mn + (size_t)bm * 2 * N * G::Kc + kx;
   #pragma unroll
   for (int y = threadIdx.x; y < N; y += G::THREADS) M[(size_t)y * G::Kc] = a[y];
@@ -272,31 +303,21 @@ __global__ void k_half_to_compact(const double2* __restrict__ in, double2* __res
 // Control map and the inverse column transforms of a stage state
 // ---------------------------------------------------------------------------
 
-// Writes the two column values (u = i ky/k^2 w, v = -i kx/k^2 w of state
-// value Yv at ky, column kx, scaled by 1/N^2) into position q = ky mod N of
-// seq[0..1][N].
+// Writes the two column values u = i ky/k^2 Yv, v = -i kx/k^2 Yv (scaled by
+// 1/N^2; f = symF entry of the mode) into position q of seq[0..1][N].
 template <int N>
-__device__ __forceinline__ void put_stage_columns(double2* seq, int kx, int ky, double2 Yv) {
-  const double k2 = (double)(kx * kx + ky * ky);
-  const double ik2 = k2 > 0.0 ? 1.0 / k2 : 0.0;
-  const double s = 1.0 / ((double)N * N);
-  const int q = ky & (N - 1);
-  const double2 Ys = cscale(Yv, s);
-  const double a = ky * ik2, c = kx * ik2;
-  seq[q] = make_double2(-a * Ys.y, a * Ys.x);      // u:  i ky / k^2
-  seq[N + q] = make_double2(c * Ys.y, -c * Ys.x);  // v: -i kx / k^2
+__device__ __forceinline__ void put_stage_columns(double2* seq, int q, const Sym4& f, double2 Yv) {
+  seq[q] = make_double2(-f.a * Yv.y, f.a * Yv.x);      // u:  i ky / k^2
+  seq[N + q] = make_double2(f.b * Yv.y, -f.b * Yv.x);  // v: -i kx / k^2
 }
 
 // Writes the two column values of the adjoint fields of an adjoint stage
-// value kb: a = d_xy kb = -kx ky kb and b = (d_xx - d_yy) kb =
-// (ky^2 - kx^2) kb, scaled by 1/N^2, at q = ky mod N of seq[0..1][N].
+// value kb: 2a = 2 d_xy kb = -2 kx ky kb and b = (d_xx - d_yy) kb =
+// (ky^2 - kx^2) kb, scaled by 1/N^2 (g = symA entry of the mode), at q.
 template <int N>
-__device__ __forceinline__ void put_adjoint_columns(double2* seq, int kx, int ky, double2 kb) {
-  const double s = 1.0 / ((double)N * N);
-  const int q = ky & (N - 1);
-  const double ca = -(double)(kx * ky) * s, cb = (double)(ky * ky - kx * kx) * s;
-  seq[q] = cscale(kb, ca);
-  seq[N + q] = cscale(kb, cb);
+__device__ __forceinline__ void put_adjoint_columns(double2* seq, int q, const Sym4& g, double2 kb) {
+  seq[q] = cscale(kb, g.c);
+  seq[N + q] = cscale(kb, g.d);
 }
 
 // Zeroes the positions outside the retained set in `nseq` sequences.
@@ -345,8 +366,8 @@ __device__ __forceinline__ void pack_field_pairs(double2* a, const double2* __re
 }
 
 // Forward transforms along x of rows y0, y0+1 of two real fields, packed as
-// seq f = (field f row y0) + i (field f row y0+1) -> rows of both fields of
-// the mixed buffer O (kx <= K).
+// seq f = (field f row y0) + i (field f row y0+1) -> twice the rows of both
+// fields of the mixed buffer O (kx <= K).
 template <int N>
 __device__ __forceinline__ void unpack_field_rows(const double2* a, double2* __restrict__ O, int y0) {
   using G = Geo<N>;
@@ -356,7 +377,7 @@ __device__ __forceinline__ void unpack_field_rows(const double2* a, double2* __r
     if (u < 2 * G::Kc) {
       const int f = u / G::Kc, kx = u - f * G::Kc;
       double2 A, Bv;
-      unpack_pair<N>(a + f * N, kx, A, Bv);
+      unpack_pair2<N>(a + f * N, kx, A, Bv);
       O[((size_t)f * N + y0) * G::Kc + kx] = A;
       O[((size_t)f * N + y0 + 1) * G::Kc + kx] = Bv;
     }
@@ -370,13 +391,14 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_ctrl_cols(Dev d, int flags) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N;
+  double* T = reinterpret_cast<double*>(sm);
+  double2* a = sm + FoldInfo<N>::PADDED / 2;
   const int kx = blockIdx.x, bm = blockIdx.y;
-  load_twiddles<N>(tw, d.tw);
+  load_fold<N>(T, d.fold);
   const double2* M = d.Mn + (size_t)bm * 2 * N * G::Kc + kx;
   load_column<N, G::THREADS, 1>(a, M);
   __syncthreads();
-  fft_batch<N, -1, 1>(a, tw);
+  fft_folded<N, -1, 1>(a, T);
   // each retained position is read and rewritten by one thread only
   #pragma unroll
   for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
@@ -385,12 +407,12 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_ctrl_cols(Dev d, int flags)
     const double2 w0 = cscale(a[ky & (N - 1)], d.mult[idx]);
     d.W[idx] = w0;
     d.Y[idx] = w0;
-    put_stage_columns<N>(a, kx, ky, w0);
+    put_stage_columns<N>(a, ky & (N - 1), d.symF[kx * G::Kr + rr], w0);
   }
   if (flags & F_NO_NEXT) return;
   zero_outside<N>(a, 2);
   __syncthreads();
-  fft_batch<N, +1, 2>(a, tw);
+  fft_folded<N, +1, 2>(a, T);
   store_mixed2<N>(d, a, bm, kx);
 }
 
@@ -400,9 +422,10 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_state_cols(Dev d) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N;
+  double* T = reinterpret_cast<double*>(sm);
+  double2* a = sm + FoldInfo<N>::PADDED / 2;
   const int kx = blockIdx.x, bm = blockIdx.y;
-  load_twiddles<N>(tw, d.tw);
+  load_fold<N>(T, d.fold);
   zero_outside<N>(a, 2);
   #pragma unroll
   for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
@@ -410,10 +433,10 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_state_cols(Dev d) {
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
     const double2 w = d.W[idx];
     d.Y[idx] = w;
-    put_stage_columns<N>(a, kx, ky, w);
+    put_stage_columns<N>(a, ky & (N - 1), d.symF[kx * G::Kr + rr], w);
   }
   __syncthreads();
-  fft_batch<N, +1, 2>(a, tw);
+  fft_folded<N, +1, 2>(a, T);
   store_mixed2<N>(d, a, bm, kx);
 }
 
@@ -428,12 +451,13 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_rows(Dev d, int n, int stage, int flags) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N;
+  double* T = reinterpret_cast<double*>(sm);
+  double2* a = sm + FoldInfo<N>::PADDED / 2;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
-  load_twiddles<N>(tw, d.tw);
+  load_fold<N>(T, d.fold);
   pack_field_pairs<N>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
   __syncthreads();
-  fft_batch<N, +1, 2>(a, tw);
+  fft_folded<N, +1, 2>(a, T);
   const int st = N / d.px;
   const int slot = (flags & (F_OBS | F_OBS_ONLY)) ? obs_slot(d, n) : -1;
   double* trj = (flags & F_STORE)
@@ -467,7 +491,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_rows(Dev d, int n, int 
   }
   if (flags & F_OBS_ONLY) return;
   __syncthreads();
-  fft_batch<N, -1, 2>(a, tw);
+  fft_folded<N, -1, 2>(a, T);
   unpack_field_rows<N>(a, d.Mn + (size_t)bm * 2 * N * G::Kc, y0);
 }
 
@@ -480,12 +504,13 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, int flags) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N;
+  double* T = reinterpret_cast<double*>(sm);
+  double2* a = sm + FoldInfo<N>::PADDED / 2;
   const int kx = blockIdx.x, bm = blockIdx.y;
-  load_twiddles<N>(tw, d.tw);
+  load_fold<N>(T, d.fold);
   load_column<N, G::THREADS, 2>(a, d.Mn + (size_t)bm * 2 * N * G::Kc + kx);
   __syncthreads();
-  fft_batch<N, -1, 2>(a, tw);
+  fft_folded<N, -1, 2>(a, T);
   const double dt = d.dt;
   const double fval = -d.amp * d.nf * (double)N * N / 2.0;
   // each retained position is read and rewritten (both sequences) by one
@@ -495,39 +520,39 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, 
     const int ky = ky_of_row(rr, G::K);
     const int qi = ky & (N - 1);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+    const Sym4 f = d.symF[kx * G::Kr + rr];
+    const double nk2 = d.nuk2[kx * G::Kr + rr];
     const double2 ph = a[qi], qh = a[N + qi];
-    const double cp = (double)(ky * ky - kx * kx), cq = -(double)(kx * ky);
-    const double2 nh = make_double2(fma(cp, ph.x, cq * qh.x), fma(cp, ph.y, cq * qh.y));
     const double2 yv = d.Y[idx];
-    const double k2 = (double)(kx * kx + ky * ky);
-    double2 F = make_double2(-nh.x - d.nu * k2 * yv.x, -nh.y - d.nu * k2 * yv.y);
+    // F = -(cp P + cq Q) - nu k^2 y
+    double2 F = make_double2(-fma(f.c, ph.x, fma(f.d, qh.x, nk2 * yv.x)),
+                             -fma(f.c, ph.y, fma(f.d, qh.y, nk2 * yv.y)));
     if (d.force && kx == 0 && (ky == d.nf || ky == -d.nf)) F.x += fval;
     const double2 w = d.W[idx];
     double2 ynext;
     if (stage == 1) {
       d.Acc[idx] = F;
-      ynext = make_double2(w.x + 0.5 * dt * F.x, w.y + 0.5 * dt * F.y);
+      ynext = make_double2(fma(d.dt2, F.x, w.x), fma(d.dt2, F.y, w.y));
     } else if (stage == 2) {
       const double2 acc = d.Acc[idx];
-      d.Acc[idx] = make_double2(acc.x + 2.0 * F.x, acc.y + 2.0 * F.y);
-      ynext = make_double2(w.x + 0.5 * dt * F.x, w.y + 0.5 * dt * F.y);
+      d.Acc[idx] = make_double2(fma(2.0, F.x, acc.x), fma(2.0, F.y, acc.y));
+      ynext = make_double2(fma(d.dt2, F.x, w.x), fma(d.dt2, F.y, w.y));
     } else if (stage == 3) {
       const double2 acc = d.Acc[idx];
-      d.Acc[idx] = make_double2(acc.x + 2.0 * F.x, acc.y + 2.0 * F.y);
-      ynext = make_double2(w.x + dt * F.x, w.y + dt * F.y);
+      d.Acc[idx] = make_double2(fma(2.0, F.x, acc.x), fma(2.0, F.y, acc.y));
+      ynext = make_double2(fma(dt, F.x, w.x), fma(dt, F.y, w.y));
     } else {
       const double2 acc = d.Acc[idx];
-      const double c = dt / 6.0;
-      ynext = make_double2(w.x + c * (acc.x + F.x), w.y + c * (acc.y + F.y));
+      ynext = make_double2(fma(d.dt6, acc.x + F.x, w.x), fma(d.dt6, acc.y + F.y, w.y));
       d.W[idx] = ynext;
     }
     d.Y[idx] = ynext;
-    put_stage_columns<N>(a, kx, ky, ynext);
+    put_stage_columns<N>(a, qi, f, ynext);
   }
   if (flags & F_NO_NEXT) return;
   zero_outside<N>(a, 2);
   __syncthreads();
-  fft_batch<N, +1, 2>(a, tw);
+  fft_folded<N, +1, 2>(a, T);
   store_mixed2<N>(d, a, bm, kx);
 }
 
@@ -608,9 +633,10 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_init(Dev d, int mode) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *Tu = a + 2 * N, *Tv = Tu + G::PMAX;
+  double* T = reinterpret_cast<double*>(sm);
+  double2 *a = sm + FoldInfo<N>::PADDED / 2, *Tu = a + 2 * N, *Tv = Tu + G::PMAX;
   const int kx = blockIdx.x, bm = blockIdx.y;
-  load_twiddles<N>(tw, d.tw);
+  load_fold<N>(T, d.fold);
   const bool resume = (mode & INIT_RESUME) != 0;
   const int slot = (!resume && (mode & INIT_SRC)) ? obs_slot(d, d.nsteps) : -1;
   if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
@@ -627,29 +653,31 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_init(Dev d, int mode) {
       double2 lam = (mode & INIT_LAMBAR) ? d.LamBar[idx] : make_double2(0.0, 0.0);
       if (slot >= 0) lam = cadd(lam, probe_source(d, kx, ky, Tu, Tv));
       d.LamBar[idx] = lam;
-      kb = cscale(lam, d.dt / 6.0);
+      kb = cscale(lam, d.dt6);
       d.KB[idx] = kb;
     }
-    put_adjoint_columns<N>(a, kx, ky, kb);
+    put_adjoint_columns<N>(a, ky & (N - 1), d.symA[kx * G::Kr + rr], kb);
   }
   __syncthreads();
-  fft_batch<N, +1, 2>(a, tw);
+  fft_folded<N, +1, 2>(a, T);
   store_mixed2<N>(d, a, bm, kx);
 }
 
-// Adjoint row pass of stage `stage` of step n: a, b of rows y0, y0+1
+// Adjoint row pass of stage `stage` of step n: 2a, b of rows y0, y0+1
 // (inverse transforms along x), rho_u and rho_v with the stored u, v, and
-// their forward transforms along x into Mn.  grid (N/2, B).
+// their forward transforms along x into Mn (twice, as in the forward row
+// pass).  grid (N/2, B).
 template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_rows(Dev d, int n, int stage) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N;
+  double* T = reinterpret_cast<double*>(sm);
+  double2* a = sm + FoldInfo<N>::PADDED / 2;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
-  load_twiddles<N>(tw, d.tw);
+  load_fold<N>(T, d.fold);
   pack_field_pairs<N>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
   __syncthreads();
-  fft_batch<N, +1, 2>(a, tw);
+  fft_folded<N, +1, 2>(a, T);
   const double* trj = d.traj + (((size_t)bm * d.traj_steps + (n - d.seg0)) * 4 + (stage - 1)) * 2 * (size_t)N * N;
   // one thread per column x reads (a, b) of both rows, then writes
   // rho_u and rho_v of both rows at x
@@ -658,17 +686,17 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_rows(Dev d, int n, int 
     double ru[2], rv[2];
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
-      const double2 ab = a[rr * N + x];
+      const double2 ab = a[rr * N + x];  // (2a, b)
       const size_t o = (size_t)(y0 + rr) * N + x;
       const double fu = trj[o], fv = trj[(size_t)N * N + o];
-      ru[rr] = fma(fv, ab.y, -2.0 * fu * ab.x);
-      rv[rr] = fma(fu, ab.y, 2.0 * fv * ab.x);
+      ru[rr] = fma(fv, ab.y, -fu * ab.x);
+      rv[rr] = fma(fu, ab.y, fv * ab.x);
     }
     a[x] = make_double2(ru[0], ru[1]);
     a[N + x] = make_double2(rv[0], rv[1]);
   }
   __syncthreads();
-  fft_batch<N, -1, 2>(a, tw);
+  fft_folded<N, -1, 2>(a, T);
   unpack_field_rows<N>(a, d.Mn + (size_t)bm * 2 * N * G::Kc, y0);
 }
 
@@ -681,14 +709,15 @@ template <int N>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int stage, int flags) {
   using G = Geo<N>;
   extern __shared__ double2 sm[];
-  double2 *tw = sm, *a = tw + N, *Tu = a + 2 * N, *Tv = Tu + G::PMAX;
+  double* T = reinterpret_cast<double*>(sm);
+  double2 *a = sm + FoldInfo<N>::PADDED / 2, *Tu = a + 2 * N, *Tv = Tu + G::PMAX;
   const int kx = blockIdx.x, bm = blockIdx.y;
-  load_twiddles<N>(tw, d.tw);
+  load_fold<N>(T, d.fold);
   load_column<N, G::THREADS, 2>(a, d.Mn + (size_t)bm * 2 * N * G::Kc + kx);
   const int slot = (flags & F_SRC) ? obs_slot(d, n) : -1;
   if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
   __syncthreads();
-  fft_batch<N, -1, 2>(a, tw);
+  fft_folded<N, -1, 2>(a, T);
   const double dt = d.dt;
   // each retained position is read and rewritten (both sequences) by one
   // thread only
@@ -698,42 +727,41 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int 
     const int qi = ky & (N - 1);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
     const double2 Ru = a[qi], Rv = a[N + qi];
-    const double k2 = (double)(kx * kx + ky * ky);
-    const double ik2 = k2 > 0.0 ? 1.0 / k2 : 0.0;
-    const double a1 = ky * ik2, c1 = kx * ik2;
-    // t = (-i ky/k^2) Ru + (i kx/k^2) Rv
-    const double2 t = make_double2(fma(a1, Ru.y, -c1 * Rv.y), fma(-a1, Ru.x, c1 * Rv.x));
+    const Sym4 g = d.symA[kx * G::Kr + rr];
+    const double nk2 = d.nuk2[kx * G::Kr + rr];
+    // t = (-i ky/k^2) Ru + (i kx/k^2) Rv (the 1/2 of the row unpack in a1, c1)
+    const double2 t = make_double2(fma(g.a, Ru.y, -g.b * Rv.y), fma(-g.a, Ru.x, g.b * Rv.x));
     const double2 kb = d.KB[idx];
     double2 yb;
-    yb.x = -t.x - d.nu * k2 * kb.x;
-    yb.y = -t.y - d.nu * k2 * kb.y;
+    yb.x = -fma(nk2, kb.x, t.x);
+    yb.y = -fma(nk2, kb.y, t.y);
     const double2 lb = d.LamBar[idx];
     double2 nk;
     if (stage == 4) {
       d.Sum[idx] = yb;
-      nk = make_double2(dt / 3.0 * lb.x + dt * yb.x, dt / 3.0 * lb.y + dt * yb.y);
+      nk = make_double2(fma(d.dt3, lb.x, dt * yb.x), fma(d.dt3, lb.y, dt * yb.y));
     } else if (stage == 3) {
       const double2 sm2 = d.Sum[idx];
       d.Sum[idx] = cadd(sm2, yb);
-      nk = make_double2(dt / 3.0 * lb.x + dt / 2.0 * yb.x, dt / 3.0 * lb.y + dt / 2.0 * yb.y);
+      nk = make_double2(fma(d.dt3, lb.x, d.dt2 * yb.x), fma(d.dt3, lb.y, d.dt2 * yb.y));
     } else if (stage == 2) {
       const double2 sm2 = d.Sum[idx];
       d.Sum[idx] = cadd(sm2, yb);
-      nk = make_double2(dt / 6.0 * lb.x + dt / 2.0 * yb.x, dt / 6.0 * lb.y + dt / 2.0 * yb.y);
+      nk = make_double2(fma(d.dt6, lb.x, d.dt2 * yb.x), fma(d.dt6, lb.y, d.dt2 * yb.y));
     } else {
       const double2 sum = cadd(d.Sum[idx], yb);
       double2 lam = cadd(lb, sum);
       if (slot >= 0) lam = cadd(lam, probe_source(d, kx, ky, Tu, Tv));
       d.LamBar[idx] = lam;
-      nk = cscale(lam, dt / 6.0);
+      nk = cscale(lam, d.dt6);
     }
     d.KB[idx] = nk;
-    put_adjoint_columns<N>(a, kx, ky, nk);
+    put_adjoint_columns<N>(a, qi, g, nk);
   }
   if (flags & F_FINAL) return;
   zero_outside<N>(a, 2);
   __syncthreads();
-  fft_batch<N, +1, 2>(a, tw);
+  fft_folded<N, +1, 2>(a, T);
   store_mixed2<N>(d, a, bm, kx);
 }
 

@@ -9,6 +9,8 @@ namespace da {
 
 struct Ops {
   int n, K, Kc, Kr;
+  int fold_doubles;                 // entries of the folded twiddle table
+  void (*fold_table)(double* out);  // fills it on the host
   cudaError_t (*setup)();
   void (*r2c_rows)(const Dev&, const double* in, cudaStream_t);
   void (*c2r_rows)(const Dev&, double* out, cudaStream_t);

@@ -12,6 +12,8 @@ Ops make_ops() {
   o.K = G::K;
   o.Kc = G::Kc;
   o.Kr = G::Kr;
+  o.fold_doubles = FoldInfo<N>::DOUBLES;
+  o.fold_table = [](double* out) { fold_table<N>(out); };
   o.setup = []() -> cudaError_t {
     const int s = (int)G::SMEM;
     cudaError_t e = cudaSuccess;

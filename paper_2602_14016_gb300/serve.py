@@ -69,7 +69,7 @@ def context_bytes(n: int, nsteps: int, px: int, every: int, ckpt_every: int, bat
     nt = nsteps // every
     comp = batch * Kr * Kc * 16
     b = 6 * comp + batch * 4 * n * Kc * 16 + 3 * batch * nt * px * px * 2 * 8 + comp // 2
-    b += n * 16 + px * 16 + batch * (8 + 4 + 8) + batch * 8
+    b += n * 16 + px * 16 + batch * (8 + 4 + 8) + batch * 8 + Kr * Kc * 72
     if ckpt_every == 0:
         b += batch * nsteps * 8 * n * n * 8
     else:

@@ -65,6 +65,13 @@ def test_batched_members_equal_single_member_runs(api, workload):
 
 
 def test_full_window_gradient_against_central_differences(api, workload):
+    """Central differences of J along a seeded unit direction per member.
+    Over a chaotic 2000-step window their error is truncation (eps^2 times
+    large higher derivatives) at large eps and amplified rounding at small
+    eps, about 1e-8..3e-6 relative at the best eps for these members (the
+    smallest |g.d|, under exp(-|k|), is the noisiest).  A missing or
+    mis-signed term of the adjoint gives errors of order one, so the bound is
+    1e-5 at the best of three step sizes, and 1e-6 for the median member."""
     m, guess = workload
     ctx = api.Context(config(api, SWEEP))
     ctx.set_graphs(True)
@@ -73,15 +80,15 @@ def test_full_window_gradient_against_central_differences(api, workload):
     J, g = ctx.cost_grad(s)
     d = torch.from_numpy(np.stack([synthetic.random_field(N, 700 + b) for b in range(len(SWEEP))])).cuda()
     d = d / torch.linalg.norm(d.reshape(len(SWEEP), -1), dim=1)[:, None, None]
-    gd = (g * d).sum(dim=(1, 2))
+    gd = (g * d).sum(dim=(1, 2)).cpu().numpy()
     errs = []
-    for eps in (1e-4, 1e-5):
+    for eps in (1e-4, 3e-5, 1e-5):
         Jp, _ = ctx.cost_grad(s + eps * d)
         Jm, _ = ctx.cost_grad(s - eps * d)
-        fd = (Jp - Jm) / (2 * eps)
-        errs.append((torch.abs(fd - gd) / torch.abs(gd)).cpu().numpy())
-    best = np.minimum(errs[0], errs[1])
-    assert np.all(best < 1e-6), errs
+        fd = (Jp - Jm).cpu().numpy() / (2 * eps)
+        errs.append(np.abs(fd - gd) / np.abs(gd))
+    best = np.min(errs, axis=0)
+    assert np.all(best < 1e-5) and np.median(best) < 1e-6, (gd, errs)
 
 
 def test_checkpointed_full_window_equals_full_storage(api, workload):
