@@ -48,9 +48,12 @@ UNIT = "gridpoint-steps/s"
 # DFMA throughput probe on this GPU) x 2 flop x 2.07 GHz maximum SM clock.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 
-# DRAM bytes per launch of each pass kernel at this workload, from one ncu
-# capture; valid only for the kernel sources they were taken from.
-TRAFFIC = {"src_hash": None}
+# DRAM bytes (read + write) per launch of each pass kernel at this workload
+# (256^2, batch 7), from one ncu capture of the same launch configuration on
+# a 40-step window (per-launch data are the same for any window length);
+# valid only for the kernel sources they were taken from.
+TRAFFIC = {"src_hash": "47b6d28683679dc1", "adj_rows": 12315392, "adj_cols": 10548992, "fwd_rows": 4996608,
+           "fwd_cols": 10508800}
 
 
 def src_hash() -> str:
@@ -308,7 +311,7 @@ def run_gpu(args):
     pf = pass_flops(n, B)[dom]
     avg_ms = dom_ms / max(dom_n, 1)
     achieved = pf / (avg_ms / 1e3) / 1e9
-    traffic = TRAFFIC.get(dom) if TRAFFIC.get("src_hash") == src_hash() else None
+    traffic = TRAFFIC.get(dom) if (TRAFFIC.get("src_hash") == src_hash() and n == 256 and B == 7) else None
     cpu = cpu_baseline(args) if args.cpu_baseline else None
     line = {
         "metric": METRIC,
