@@ -146,7 +146,7 @@ template <> struct Plan<16> { using two = Radices<4, 4>; using one = Radices<4, 
 template <> struct Plan<32> { using two = Radices<4, 8>; using one = Radices<4, 8>; static constexpr int threads = 32; };
 template <> struct Plan<64> { using two = Radices<4, 4, 4>; using one = Radices<4, 4, 4>; static constexpr int threads = 32; };
 template <> struct Plan<128> { using two = Radices<4, 4, 8>; using one = Radices<4, 4, 8>; static constexpr int threads = 64; };
-template <> struct Plan<256> { using two = Radices<8, 8, 4>; using one = Radices<8, 8, 4>; static constexpr int threads = 64; };
+template <> struct Plan<256> { using two = Radices<4, 4, 4, 4>; using one = Radices<4, 4, 4, 4>; static constexpr int threads = 128; };
 template <> struct Plan<512> { using two = Radices<8, 8, 8>; using one = Radices<8, 8, 8>; static constexpr int threads = 128; };
 template <> struct Plan<1024> { using two = Radices<16, 8, 8>; using one = Radices<16, 8, 8>; static constexpr int threads = 256; };
 

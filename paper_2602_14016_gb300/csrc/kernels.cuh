@@ -105,6 +105,9 @@ struct Geo {
   // probe sums
   static constexpr int PMAX = 64;
   static constexpr size_t SMEM = sizeof(double) * FoldInfo<N>::PADDED + sizeof(double2) * (2 * N + 2 * PMAX);
+  // column passes load their epilogue inputs before the transforms (about
+  // 60 more registers a thread) where a CTA is at most 128 threads
+  static constexpr bool PREFETCH = THREADS <= 128;
 };
 
 __device__ __forceinline__ int ky_of_row(int r, int K) { return r <= K ? r : r - (2 * K + 1); }
@@ -509,45 +512,64 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, 
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_fold<N>(T, d.fold);
   load_column<N, G::THREADS, 2>(a, d.Mn + (size_t)bm * 2 * N * G::Kc + kx);
+  // the epilogue's inputs for this thread's modes; where registers allow
+  // (G::PREFETCH), loaded now so that their latency hides behind the
+  // column transforms
+  constexpr int MT = (G::Kr + G::THREADS - 1) / G::THREADS;
+  double2 yv[MT], wv[MT], accv[MT];
+  Sym4 f[MT];
+  double nk2[MT];
+  auto load_inputs = [&](int t) {
+    const int rr = threadIdx.x + t * G::THREADS;
+    if (rr < G::Kr) {
+      const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+      yv[t] = d.Y[idx];
+      wv[t] = d.W[idx];
+      accv[t] = stage > 1 ? d.Acc[idx] : make_double2(0.0, 0.0);
+      f[t] = d.symF[kx * G::Kr + rr];
+      nk2[t] = d.nuk2[kx * G::Kr + rr];
+    }
+  };
+  if constexpr (G::PREFETCH) {
+#pragma unroll
+    for (int t = 0; t < MT; ++t) load_inputs(t);
+  }
   __syncthreads();
   fft_folded<N, -1, 2>(a, T);
   const double dt = d.dt;
   const double fval = -d.amp * d.nf * (double)N * N / 2.0;
   // each retained position is read and rewritten (both sequences) by one
   // thread only
-  #pragma unroll
-  for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
+#pragma unroll
+  for (int t = 0; t < MT; ++t) {
+    const int rr = threadIdx.x + t * G::THREADS;
+    if (rr >= G::Kr) break;
+    if constexpr (!G::PREFETCH) load_inputs(t);
     const int ky = ky_of_row(rr, G::K);
     const int qi = ky & (N - 1);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
-    const Sym4 f = d.symF[kx * G::Kr + rr];
-    const double nk2 = d.nuk2[kx * G::Kr + rr];
     const double2 ph = a[qi], qh = a[N + qi];
-    const double2 yv = d.Y[idx];
     // F = -(cp P + cq Q) - nu k^2 y
-    double2 F = make_double2(-fma(f.c, ph.x, fma(f.d, qh.x, nk2 * yv.x)),
-                             -fma(f.c, ph.y, fma(f.d, qh.y, nk2 * yv.y)));
+    double2 F = make_double2(-fma(f[t].c, ph.x, fma(f[t].d, qh.x, nk2[t] * yv[t].x)),
+                             -fma(f[t].c, ph.y, fma(f[t].d, qh.y, nk2[t] * yv[t].y)));
     if (d.force && kx == 0 && (ky == d.nf || ky == -d.nf)) F.x += fval;
-    const double2 w = d.W[idx];
+    const double2 w = wv[t], acc = accv[t];
     double2 ynext;
     if (stage == 1) {
       d.Acc[idx] = F;
       ynext = make_double2(fma(d.dt2, F.x, w.x), fma(d.dt2, F.y, w.y));
     } else if (stage == 2) {
-      const double2 acc = d.Acc[idx];
       d.Acc[idx] = make_double2(fma(2.0, F.x, acc.x), fma(2.0, F.y, acc.y));
       ynext = make_double2(fma(d.dt2, F.x, w.x), fma(d.dt2, F.y, w.y));
     } else if (stage == 3) {
-      const double2 acc = d.Acc[idx];
       d.Acc[idx] = make_double2(fma(2.0, F.x, acc.x), fma(2.0, F.y, acc.y));
       ynext = make_double2(fma(dt, F.x, w.x), fma(dt, F.y, w.y));
     } else {
-      const double2 acc = d.Acc[idx];
       ynext = make_double2(fma(d.dt6, acc.x + F.x, w.x), fma(d.dt6, acc.y + F.y, w.y));
       d.W[idx] = ynext;
     }
     d.Y[idx] = ynext;
-    put_stage_columns<N>(a, qi, f, ynext);
+    put_stage_columns<N>(a, qi, f[t], ynext);
   }
   if (flags & F_NO_NEXT) return;
   zero_outside<N>(a, 2);
@@ -714,6 +736,27 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int 
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_fold<N>(T, d.fold);
   load_column<N, G::THREADS, 2>(a, d.Mn + (size_t)bm * 2 * N * G::Kc + kx);
+  // the epilogue's inputs for this thread's modes (before the column
+  // transforms where registers allow, as in k_fwd_cols)
+  constexpr int MT = (G::Kr + G::THREADS - 1) / G::THREADS;
+  double2 kbv[MT], lbv[MT], sumv[MT];
+  Sym4 g[MT];
+  double nk2[MT];
+  auto load_inputs = [&](int t) {
+    const int rr = threadIdx.x + t * G::THREADS;
+    if (rr < G::Kr) {
+      const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+      kbv[t] = d.KB[idx];
+      lbv[t] = d.LamBar[idx];
+      sumv[t] = stage < 4 ? d.Sum[idx] : make_double2(0.0, 0.0);
+      g[t] = d.symA[kx * G::Kr + rr];
+      nk2[t] = d.nuk2[kx * G::Kr + rr];
+    }
+  };
+  if constexpr (G::PREFETCH) {
+#pragma unroll
+    for (int t = 0; t < MT; ++t) load_inputs(t);
+  }
   const int slot = (flags & F_SRC) ? obs_slot(d, n) : -1;
   if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
   __syncthreads();
@@ -721,42 +764,40 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int 
   const double dt = d.dt;
   // each retained position is read and rewritten (both sequences) by one
   // thread only
-  #pragma unroll
-  for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
+#pragma unroll
+  for (int t = 0; t < MT; ++t) {
+    const int rr = threadIdx.x + t * G::THREADS;
+    if (rr >= G::Kr) break;
+    if constexpr (!G::PREFETCH) load_inputs(t);
     const int ky = ky_of_row(rr, G::K);
     const int qi = ky & (N - 1);
     const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
     const double2 Ru = a[qi], Rv = a[N + qi];
-    const Sym4 g = d.symA[kx * G::Kr + rr];
-    const double nk2 = d.nuk2[kx * G::Kr + rr];
     // t = (-i ky/k^2) Ru + (i kx/k^2) Rv (the 1/2 of the row unpack in a1, c1)
-    const double2 t = make_double2(fma(g.a, Ru.y, -g.b * Rv.y), fma(-g.a, Ru.x, g.b * Rv.x));
-    const double2 kb = d.KB[idx];
+    const double2 tt = make_double2(fma(g[t].a, Ru.y, -g[t].b * Rv.y), fma(-g[t].a, Ru.x, g[t].b * Rv.x));
+    const double2 kb = kbv[t], lb = lbv[t];
     double2 yb;
-    yb.x = -fma(nk2, kb.x, t.x);
-    yb.y = -fma(nk2, kb.y, t.y);
-    const double2 lb = d.LamBar[idx];
+    yb.x = -fma(nk2[t], kb.x, tt.x);
+    yb.y = -fma(nk2[t], kb.y, tt.y);
     double2 nk;
     if (stage == 4) {
       d.Sum[idx] = yb;
       nk = make_double2(fma(d.dt3, lb.x, dt * yb.x), fma(d.dt3, lb.y, dt * yb.y));
     } else if (stage == 3) {
-      const double2 sm2 = d.Sum[idx];
-      d.Sum[idx] = cadd(sm2, yb);
+      d.Sum[idx] = cadd(sumv[t], yb);
       nk = make_double2(fma(d.dt3, lb.x, d.dt2 * yb.x), fma(d.dt3, lb.y, d.dt2 * yb.y));
     } else if (stage == 2) {
-      const double2 sm2 = d.Sum[idx];
-      d.Sum[idx] = cadd(sm2, yb);
+      d.Sum[idx] = cadd(sumv[t], yb);
       nk = make_double2(fma(d.dt6, lb.x, d.dt2 * yb.x), fma(d.dt6, lb.y, d.dt2 * yb.y));
     } else {
-      const double2 sum = cadd(d.Sum[idx], yb);
+      const double2 sum = cadd(sumv[t], yb);
       double2 lam = cadd(lb, sum);
       if (slot >= 0) lam = cadd(lam, probe_source(d, kx, ky, Tu, Tv));
       d.LamBar[idx] = lam;
       nk = cscale(lam, d.dt6);
     }
     d.KB[idx] = nk;
-    put_adjoint_columns<N>(a, qi, g, nk);
+    put_adjoint_columns<N>(a, qi, g[t], nk);
   }
   if (flags & F_FINAL) return;
   zero_outside<N>(a, 2);
