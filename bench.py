@@ -474,7 +474,7 @@ def main():
     ap.add_argument("--ens-ckpt", type=int, default=25)
     ap.add_argument("--ag-n", type=int, default=512)
     ap.add_argument("--ag-steps", type=int, default=4000)
-    ap.add_argument("--ag-dirs", type=int, default=20)
+    ap.add_argument("--ag-dirs", type=int, default=8)
     ap.add_argument("--rates", type=float, nargs="+", default=[2.0, 10.0])
     ap.add_argument("--serve-jobs", type=int, default=16)
     ap.add_argument("--slots", type=int, default=4)

@@ -118,10 +118,13 @@ def fit_growth_rates(tau: np.ndarray, energy: np.ndarray, skip: float = 0.3) -> 
 # Differentiable Kolmogorov window
 # ---------------------------------------------------------------------------
 
-def autograd_check(api, torch, n=512, nsteps=4000, dt=1e-3, nu=1 / 200, nf=4, ckpt_every=64, directions=20,
-                   eps=1e-6, px=16, every=40, seed=3):
+def autograd_check(api, torch, n=512, nsteps=4000, dt=1e-3, nu=1 / 200, nf=4, ckpt_every=64, directions=8,
+                   eps=(1e-4, 1e-5, 1e-6), px=16, every=40, seed=3):
     """Gradient of a torch loss through the autograd wrapper against central
-    finite differences of the same loss along seeded random directions."""
+    finite differences of the same loss along seeded random directions, at
+    several step sizes: over a long chaotic window the difference quotient is
+    truncation-limited at large steps and rounding-limited at small ones, so
+    the agreement is reported per step size and at the best one."""
     from . import autograd as ag
 
     cfg = api.Config(n=n, nsteps=nsteps, dt=dt, nu=nu, forcing="kolmogorov", nf=nf, px=px, every=every,
@@ -140,25 +143,21 @@ def autograd_check(api, torch, n=512, nsteps=4000, dt=1e-3, nu=1 / 200, nf=4, ck
     torch.cuda.synchronize()
     t_grad = time.perf_counter() - t0
     g = s.grad.detach()
-    Lval = float(L.detach())
-    errs, floors = [], []
+    errs = np.zeros((len(eps), directions))
     for k in range(directions):
         d = torch.from_numpy(synthetic.random_field(n, 9000 + k)[None]).cuda()
         d = d / torch.linalg.norm(d)
-        Lp = ag.misfit(ctx.forward(s0 + eps * d)[1], m).sum().item()
-        Lm = ag.misfit(ctx.forward(s0 - eps * d)[1], m).sum().item()
-        fd = (Lp - Lm) / (2 * eps)
         gd = float((g * d).sum())
-        errs.append(abs(fd - gd) / max(abs(gd), 1e-300))
-        # rounding floor of the difference quotient: a few ulps of L over 2 eps
-        floors.append(4 * np.finfo(float).eps * abs(Lval) / (2 * eps) / max(abs(gd), 1e-300))
-    errs, floors = np.array(errs), np.array(floors)
+        for i, e in enumerate(eps):
+            Lp = ag.misfit(ctx.forward(s0 + e * d)[1], m).sum().item()
+            Lm = ag.misfit(ctx.forward(s0 - e * d)[1], m).sum().item()
+            errs[i, k] = abs((Lp - Lm) / (2 * e) - gd) / max(abs(gd), 1e-300)
+    best = errs.min(axis=0)
     out = {"n": n, "nsteps": nsteps, "ckpt_every": ckpt_every, "device_bytes": ctx.device_bytes,
-           "full_storage_bytes": nsteps * 8 * n * n * 8, "loss": Lval, "grad_seconds": t_grad,
-           "fd_rel_err_max": float(errs.max()), "fd_rel_err_median": float(np.median(errs)),
-           "fd_rounding_floor_median": float(np.median(floors)),
-           "directions_within_10x_floor_or_1e-6": int(np.sum(errs <= np.maximum(10 * floors, 1e-6))),
-           "directions": directions, "eps": eps}
+           "full_storage_bytes": nsteps * 8 * n * n * 8, "loss": float(L.detach()), "grad_seconds": t_grad,
+           "directions": directions, "eps": list(eps),
+           "fd_rel_err_median_per_eps": [float(np.median(r)) for r in errs],
+           "fd_rel_err_best_eps_median": float(np.median(best)), "fd_rel_err_best_eps_max": float(best.max())}
     ctx.close()
     return out
 
