@@ -7,14 +7,17 @@
 // in registers and stores them to y[(i - i mod L) R + i mod L + m L].  After
 // the last stage (L = N) the output is in natural order.  Stages work in
 // place: every thread holds its butterfly in registers across a barrier, so
-// one buffer of F sequences suffices.  Twiddles come from a per-N table of
-// W_N^t = exp(-2 pi i t / N) in shared memory; the inverse sign uses the
-// conjugate.  The R-point DFTs (R = 4, 8, 16) are written out by even/odd
-// splitting so that multiplications by +-i and +-1 cost nothing.
+// one buffer of F sequences suffices.  The R-point DFTs (R = 4, 8, 16) are
+// written out by even/odd splitting so that multiplications by +-i and +-1
+// cost nothing.
 //
-// GB300's FP64 pipe is the bottleneck of every kernel here (about 2 DFMA per
-// clock per SM), so the engine counts FP64 instructions: complex products
-// use two FMAs and two multiplies, twiddles are loaded rather than computed.
+// GB300's FP64 pipe is the bottleneck of every kernel here (about 1.6 FP64
+// instructions per clock per SM for this mix), so the engine counts FP64
+// instructions.  The pass kernels use fft_folded: the twiddles' cosines are
+// folded into the butterflies' FMAs (see "Folded twiddles" below), from a
+// per-N table in shared memory.  fft_batch, with a plain table of
+// W_N^t = exp(-2 pi i t / N) (conjugated for the inverse sign), serves the
+// allocation-free control map, whose scratch is static.
 #pragma once
 #include <cuda_runtime.h>
 
