@@ -203,6 +203,11 @@ def run_gpu(args):
     cfg = api.Config(n=n, nsteps=nsteps, dt=W["dt"], nu=W["nu"], forcing=W["forcing"], amp=W["amp"], nf=W["nf"],
                      px=W["px"], every=W["every"], kernels=[api.KernelSpec(k, a) for k, a in kernels])
     ctx = api.Context(cfg, device)
+    # FFT plan: the autotuner times each variant on this batch (outside the
+    # timed region) and keeps the fastest
+    tune = {"chosen": ctx.plan, "ms_per_step": None}
+    if args.tune_steps > 0:
+        tune["chosen"], tune["ms_per_step"] = ctx.autotune(args.tune_steps)
     ctx.set_observations(torch.from_numpy(m).to(device))
     s = ctx.control_from_omega(torch.from_numpy(w_guess).to(device))
     stream = torch.cuda.current_stream()
@@ -295,6 +300,8 @@ def run_gpu(args):
         del ctx
         torch.cuda.empty_cache()
         ctx1 = api.Context(cfg1, device)
+        if args.tune_steps > 0:
+            ctx1.autotune(args.tune_steps)
         ctx1.set_observations(torch.from_numpy(m[:1]).to(device))
         s1 = [ctx1.control_from_omega(torch.from_numpy(w_guess[:1]).to(device))]
         ctx1.cost_grad(s1[0])
@@ -350,6 +357,7 @@ def run_gpu(args):
         "achieved_gflops_step": value * flops_per_gridpoint_step(n) / 1e9,
         "cpu_baseline": cpu,
         "plain_path": plain,
+        "fft_plan": tune,
         "clocks": clk.summary(),
         "J_mean": float(np.mean(J.cpu().numpy())),
     }
@@ -446,18 +454,21 @@ def run_workload(args):
 
         summary = {}
         for rate in args.rates:
-            jobs = workloads.serving_jobs(api, torch, args.serve_jobs, rate, seed=7)
+            mix = dict(grids=tuple(args.serve_grids), weights=tuple(args.serve_weights), steps=tuple(args.serve_steps),
+                       iters=args.serve_iters)
+            jobs = workloads.serving_jobs(api, torch, args.serve_jobs, rate, seed=7, **mix)
             free = torch.cuda.mem_get_info()[0]
             srv = serve.Server(serve.CudaExecutor(), memory_budget=int(0.6 * free), slots=args.slots,
                                job_cap=int(0.6 * free / args.slots))
             out = srv.run(jobs)
-            base_jobs = workloads.serving_jobs(api, torch, args.serve_jobs, rate, seed=7)
+            base_jobs = workloads.serving_jobs(api, torch, args.serve_jobs, rate, seed=7, **mix)
             base = serve.Server(serve.CudaExecutor(), memory_budget=int(0.6 * free), slots=1,
                                 job_cap=int(0.6 * free / args.slots)).run(base_jobs)
             summary[str(rate)] = {"continuous": out, "one_job_at_a_time": base}
         line.update({"metric": "served solves/s, p50/p99 latency", "rates": summary,
-                     "config": {"jobs": args.serve_jobs, "slots": args.slots, "grids": [128, 256, 512],
-                                "horizon_steps": [200, 600], "lbfgs_iters": 5}})
+                     "config": {"jobs": args.serve_jobs, "slots": args.slots, "grids": args.serve_grids,
+                                "grid_weights": args.serve_weights, "horizon_steps": args.serve_steps,
+                                "lbfgs_iters": args.serve_iters}})
     print(json.dumps(line), flush=True)
 
 
@@ -472,6 +483,7 @@ def main():
     ap.add_argument("--roofline-class", default=None, choices=["fwd_rows", "fwd_cols", "adj_rows", "adj_cols"])
     ap.add_argument("--roofline-evals", type=int, default=1)
     ap.add_argument("--no-graphs", dest="graphs", action="store_false")
+    ap.add_argument("--tune-steps", type=int, default=8, help="RK steps per plan variant in the autotuner (0: off)")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "autograd", "serve"],
                     help="sweep: the headline workload above; the others print their own line")
     ap.add_argument("--ens256", type=int, default=256)
@@ -484,6 +496,13 @@ def main():
     ap.add_argument("--rates", type=float, nargs="+", default=[2.0, 10.0])
     ap.add_argument("--serve-jobs", type=int, default=16)
     ap.add_argument("--slots", type=int, default=4)
+    # job mix; the defaults are a scaled-down mix that a run finishes in
+    # minutes, the full one is --serve-grids 128 256 512 1024
+    # --serve-weights 0.4 0.3 0.2 0.1 --serve-steps 500 4000 --serve-iters 30
+    ap.add_argument("--serve-grids", type=int, nargs="+", default=[128, 256, 512])
+    ap.add_argument("--serve-weights", type=float, nargs="+", default=[0.5, 0.35, 0.15])
+    ap.add_argument("--serve-steps", type=int, nargs=2, default=[200, 600])
+    ap.add_argument("--serve-iters", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-plain", dest="plain", action="store_false")

@@ -169,6 +169,37 @@ da_status da_vjp(da_ctx* ctx, const double* dobs, const double* dwT, double* gra
  * bypasses the graph.  The first call must not itself be inside a capture. */
 da_status da_set_graphs(da_ctx* ctx, int enable);
 
+/* FFT plan variants (no counterpart in the paper, whose solver is not
+ * FFT-based on GPUs): each grid size n has da_plan_count(n) variants of the
+ * radix schedule and CTA width of the pass kernels (0 if n is not a
+ * supported size).  All variants compute the same transforms; results
+ * differ only by rounding.  A context starts on variant 0, or on the variant
+ * da_autotune last chose in this process for the same n and batch. */
+int da_plan_count(int n);
+
+/* The context's current plan variant (-1 for a NULL ctx). */
+int da_get_plan(const da_ctx* ctx);
+
+/* Switches to plan variant `variant` (DA_EINVAL if out of range).  Waits
+ * for all work on the device first (cudaDeviceSynchronize), since work in
+ * flight may use the context's twiddle table.  Drops a captured graph and
+ * any stored forward trajectory (call da_forward or da_cost_grad again
+ * before da_vjp). */
+da_status da_set_plan(da_ctx* ctx, int variant);
+
+/* Autotuner: for each plan variant of the context's n, runs one warm-up and
+ * `steps` timed RK steps of the forward and (when stage fields are stored)
+ * adjoint pass kernels over the context's own batch, on zeroed working
+ * buffers, timed with CUDA events; switches the context to the fastest and
+ * records the choice for later contexts of the same n and batch in this
+ * process.  chosen (nullable): HOST int, the variant taken; ms_per_step
+ * (nullable): HOST double[da_plan_count(n)], the measured milliseconds per
+ * step of each variant.  Synchronous (it first waits for all work on the
+ * device, then runs on a stream of its own); it overwrites the context's state and
+ * stored trajectory, so call it before the evaluations (observations set by
+ * da_set_observations are kept).  DA_EINVAL for steps < 1. */
+da_status da_autotune(da_ctx* ctx, int steps, int* chosen, double* ms_per_step);
+
 /* Optional extra outputs of the last da_cost_grad / da_adjoint_terminal on
  * this context: lam0 [batch][n][n/2+1] complex, the DFT of grad_{w0} J
  * (the physical adjoint at t = 0, Eq. 12); filtered [batch][n][n] the

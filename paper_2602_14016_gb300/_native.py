@@ -20,7 +20,8 @@ STATUS_NAMES = {0: "DA_OK", 1: "DA_EINVAL", 2: "DA_ENOMEM", 3: "DA_ECUDA", 4: "D
 KERNEL_KINDS = {"identity": 0, "exp_abs": 1, "frac": 2, "exp_sq": 3, "table": 4}
 
 # Entry points declared in include/da.h, in order.
-EXPORTS = ("da_create", "da_set_sobolev", "da_set_graphs", "da_set_observations", "da_forward", "da_cost_grad", "da_vjp", "da_last_adjoint",
+EXPORTS = ("da_create", "da_set_sobolev", "da_set_graphs", "da_plan_count", "da_get_plan", "da_set_plan", "da_autotune",
+           "da_set_observations", "da_forward", "da_cost_grad", "da_vjp", "da_last_adjoint",
            "da_adjoint_terminal", "da_adjoint_spectra", "da_num_shells", "da_assimilate", "da_omega_from_control", "da_control_from_omega",
            "da_omega_from_control_static", "da_num_obs_times", "da_device_bytes", "da_launch_count",
            "da_time_kernels", "da_kernel_time", "da_last_error", "da_destroy")
@@ -76,6 +77,10 @@ def load(path: str = LIB_PATH):
                               ctypes.POINTER(ObsOperator), ctypes.POINTER(Kernel)]),
             "da_set_sobolev": (I, [C, D]),
             "da_set_graphs": (I, [C, I]),
+            "da_plan_count": (I, [I]),
+            "da_get_plan": (I, [C]),
+            "da_set_plan": (I, [C, I]),
+            "da_autotune": (I, [C, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
             "da_set_observations": (I, [C, P, P]),
             "da_forward": (I, [C, P, P, P, P]),
             "da_cost_grad": (I, [C, P, P, P, P]),

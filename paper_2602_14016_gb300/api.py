@@ -127,6 +127,24 @@ class Context:
         self._check(self.lib.da_forward(self.ctx, _ptr(s), _ptr(torch.view_as_real(wT)), _ptr(obs), _stream(stream)))
         return wT, obs
 
+    @property
+    def plan(self) -> int:
+        """Current FFT plan variant of the pass kernels."""
+        return int(self.lib.da_get_plan(self.ctx))
+
+    def set_plan(self, variant: int) -> None:
+        self._check(self.lib.da_set_plan(self.ctx, int(variant)))
+
+    def autotune(self, steps: int = 8):
+        """Time every FFT plan variant of this grid on this batch and keep the
+        fastest (also for later contexts of the same grid and batch).
+        Returns (chosen variant, [ms per RK step of each variant])."""
+        nv = int(self.lib.da_plan_count(self.cfg.n))
+        chosen = ctypes.c_int(-1)
+        ms = (ctypes.c_double * nv)()
+        self._check(self.lib.da_autotune(self.ctx, int(steps), ctypes.byref(chosen), ms))
+        return chosen.value, [float(x) for x in ms]
+
     def cost_grad(self, s: torch.Tensor, stream=None, J_on_device: bool = True):
         """(J [B], grad_s [B, n, n])."""
         s = s.contiguous()

@@ -8,7 +8,10 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/da.h"
@@ -122,6 +125,11 @@ static da_status dalloc(da_ctx* c, T** p, size_t count) {
     snprintf(buf, sizeof buf, "cudaMalloc of %.3f GB failed: %s", count * sizeof(T) / 1e9, cudaGetErrorString(e));
     return fail(c, DA_ENOMEM, buf);
   }
+#ifdef DA_POISON_ALLOCATIONS
+  // debugging builds: every fresh allocation holds NaNs (0xff bytes), so a
+  // read of device memory that nothing wrote shows up as NaN in the results
+  cudaMemset(v, 0xff, count * sizeof(T));
+#endif
   c->allocs.push_back(v);
   c->bytes += count * sizeof(T);
   *p = static_cast<T*>(v);
@@ -139,6 +147,17 @@ static std::vector<double2> roots_of_unity(int m) {
   return w;
 }
 
+// Plan variant chosen by the autotuner per (grid size, batch), for the
+// contexts created afterwards in this process.
+static std::mutex g_plan_mu;
+static std::map<std::pair<int, int>, int> g_plan_choice;
+
+static int cached_plan(int n, int B) {
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  auto it = g_plan_choice.find({n, B});
+  return it == g_plan_choice.end() ? 0 : it->second;
+}
+
 static int obs_slot_host(const da_ctx* c, int k) {
   if (k == 0) return c->obs.include_t0 ? 0 : -1;
   if (k % c->obs.every) return -1;
@@ -151,8 +170,8 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
   *out = nullptr;
   if (!grid || !obs || !kernels) return fail(nullptr, DA_EINVAL, "grid, obs and kernels must not be NULL");
   const int n = grid->n;
-  const Ops* ops = da::ops_for(n);
-  if (!ops) return fail(nullptr, DA_EINVAL, "n must be a power of two in [16, 1024]");
+  if (!da::ops_for(n)) return fail(nullptr, DA_EINVAL, "n must be a power of two in [16, 1024]");
+  const Ops* ops = da::ops_for(n, grid->batch >= 1 ? cached_plan(n, grid->batch) : 0);
   if (grid->L != 0.0 && std::fabs(grid->L - 2.0 * M_PI) > 1e-12) return fail(nullptr, DA_EINVAL, "L must be 2 pi");
   if (!(grid->dt > 0.0) || !std::isfinite(grid->dt)) return fail(nullptr, DA_EINVAL, "dt must be positive");
   if (grid->nsteps < 1) return fail(nullptr, DA_EINVAL, "nsteps must be >= 1");
@@ -222,7 +241,9 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
   A(dalloc(c, &d.res, B * c->nt * P2 * 2));
   A(dalloc(c, &d.J, B));
   A(dalloc(c, (double**)&d.mult, comp));
-  A(dalloc(c, (double**)&d.fold, (size_t)ops->fold_doubles));
+  size_t fold_max = 0;  // room for the folded table of any plan variant
+  for (int v = 0; v < da::plan_count(n); ++v) fold_max = std::max(fold_max, (size_t)da::ops_for(n, v)->fold_doubles);
+  A(dalloc(c, (double**)&d.fold, fold_max));
   A(dalloc(c, (double2**)&d.twP, (size_t)c->P));
   A(dalloc(c, (da::Sym4**)&d.symF, comp / B));
   A(dalloc(c, (da::Sym4**)&d.symA, comp / B));
@@ -577,6 +598,124 @@ extern "C" da_status da_set_graphs(da_ctx* c, int enable) {
     DA_TRY_CUDA(c, cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
   }
   c->use_graph = true;
+  return DA_OK;
+}
+
+// Switches the context's pass kernels to plan variant v: launchers, folded
+// twiddle table, shared-memory attributes.  A captured graph holds the old
+// kernels and is dropped; a stored forward trajectory is invalidated.
+static da_status set_plan(da_ctx* c, int v) {
+  const Ops* o = da::ops_for(c->n, v);
+  if (!o) return fail(c, DA_EINVAL, "plan variant out of range (da_plan_count)");
+  if (o == c->ops) return DA_OK;
+  std::vector<double> fold(o->fold_doubles);
+  o->fold_table(fold.data());
+  DA_TRY_CUDA(c, cudaMemcpy((void*)c->dev.fold, fold.data(), fold.size() * sizeof(double), cudaMemcpyHostToDevice));
+  DA_TRY_CUDA(c, o->setup());
+  c->ops = o;
+  if (c->cg_exec) {
+    cudaGraphExecDestroy(c->cg_exec);
+    c->cg_exec = nullptr;
+  }
+  c->have_fwd = false;
+  return DA_OK;
+}
+
+extern "C" int da_plan_count(int n) { return da::ops_for(n) ? da::plan_count(n) : 0; }
+
+extern "C" int da_get_plan(const da_ctx* c) { return c ? c->ops->variant : -1; }
+
+extern "C" da_status da_set_plan(da_ctx* c, int variant) {
+  if (!c) return fail(c, DA_EINVAL, "ctx must not be NULL");
+  // the folded table and the launchers change under any work in flight
+  DA_TRY_CUDA(c, cudaDeviceSynchronize());
+  return set_plan(c, variant);
+}
+
+// Zeroes the working state that the tuning passes run over.
+static da_status clear_state(da_ctx* c, cudaStream_t st) {
+  const Dev& d = c->dev;
+  const size_t comp = (size_t)c->B * c->ops->Kr * c->ops->Kc * sizeof(double2);
+  const size_t mixed = (size_t)c->B * 2 * c->n * c->ops->Kc * sizeof(double2);
+  for (void* p : {(void*)d.W, (void*)d.Acc, (void*)d.Y, (void*)d.KB, (void*)d.LamBar, (void*)d.Sum})
+    DA_TRY_CUDA(c, cudaMemsetAsync(p, 0, comp, st));
+  DA_TRY_CUDA(c, cudaMemsetAsync(d.Mx, 0, mixed, st));
+  DA_TRY_CUDA(c, cudaMemsetAsync(d.Mn, 0, mixed, st));
+  return DA_OK;
+}
+
+// `steps` RK steps of the pass kernels (forward, and the adjoint when the
+// context stores stage fields) over whatever the working buffers hold.
+static da_status tuning_steps(da_ctx* c, int steps, cudaStream_t st) {
+  const Ops* o = c->ops;
+  Dev& d = c->dev;
+  const bool store = d.traj != nullptr;
+  d.seg0 = 0;
+  for (int i = 0; i < steps; ++i) {
+    const int k = store ? i % d.traj_steps : 0;
+    for (int j = 1; j <= 4; ++j) {
+      o->fwd_rows(d, k, j, store ? da::F_STORE : 0, st);
+      o->fwd_cols(d, j, 0, st);
+    }
+    if (store)
+      for (int j = 4; j >= 1; --j) {
+        o->adj_rows(d, k, j, st);
+        o->adj_cols(d, k, j, 0, st);
+      }
+    da_status r = check_launch(c, store ? 16 : 8);
+    if (r) return r;
+  }
+  return DA_OK;
+}
+
+extern "C" da_status da_autotune(da_ctx* c, int steps, int* chosen, double* ms_per_step) {
+  if (!c) return fail(c, DA_EINVAL, "ctx must not be NULL");
+  if (steps < 1) return fail(c, DA_EINVAL, "steps must be >= 1");
+  // the tuning passes overwrite the working state: let every evaluation in
+  // flight on any stream finish first
+  DA_TRY_CUDA(c, cudaDeviceSynchronize());
+  cudaStream_t st = nullptr;
+  DA_TRY_CUDA(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  da_status r = DA_OK;
+  int best = 0;
+  float best_ms = 0.f;
+  auto cuda = [&](cudaError_t e, const char* what) {
+    if (r == DA_OK && e != cudaSuccess) r = fail(c, DA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  cuda(cudaEventCreate(&e0), "event");
+  cuda(cudaEventCreate(&e1), "event");
+  for (int v = 0; r == DA_OK && v < da::plan_count(c->n); ++v) {
+    if ((r = set_plan(c, v))) break;
+    if ((r = clear_state(c, st))) break;
+    if ((r = tuning_steps(c, 1, st))) break;  // warm-up
+    cuda(cudaEventRecord(e0, st), "event record");
+    if (r || (r = tuning_steps(c, steps, st))) break;
+    cuda(cudaEventRecord(e1, st), "event record");
+    cuda(cudaEventSynchronize(e1), "event synchronize");
+    float ms = 0.f;
+    cuda(cudaEventElapsedTime(&ms, e0, e1), "event elapsed time");
+    if (r) break;
+    ms /= steps;
+    if (ms_per_step) ms_per_step[v] = ms;
+    if (v == 0 || ms < best_ms) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  if (r == DA_OK) r = set_plan(c, best);
+  if (r == DA_OK) r = clear_state(c, st);
+  if (r == DA_OK) cuda(cudaStreamSynchronize(st), "stream synchronize");
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  if (r) return r;
+  {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    g_plan_choice[{c->n, c->B}] = best;
+  }
+  c->have_fwd = false;
+  if (chosen) *chosen = best;
   return DA_OK;
 }
 

@@ -139,23 +139,40 @@ __device__ __forceinline__ void dftR(double2* a) {
 template <int... Rs>
 struct Radices {};
 
-// Plan for two concurrent transforms (the pass kernels) and for a single
-// transform (control and gradient maps), with the CTA width they run on.
-// Wide radices keep the FP64 instruction count low; the width is chosen so
-// that the stages of the two-transform plan fill whole warps (a stage with
-// more butterflies than threads gives each thread several).
-template <int N> struct Plan;
-template <> struct Plan<16> { using two = Radices<4, 4>; using one = Radices<4, 4>; static constexpr int threads = 32; };
-template <> struct Plan<32> { using two = Radices<4, 8>; using one = Radices<4, 8>; static constexpr int threads = 32; };
-template <> struct Plan<64> { using two = Radices<4, 4, 4>; using one = Radices<4, 4, 4>; static constexpr int threads = 32; };
-template <> struct Plan<128> { using two = Radices<4, 4, 8>; using one = Radices<4, 4, 8>; static constexpr int threads = 64; };
-template <> struct Plan<256> { using two = Radices<4, 4, 4, 4>; using one = Radices<4, 4, 4, 4>; static constexpr int threads = 128; };
-template <> struct Plan<512> { using two = Radices<8, 8, 8>; using one = Radices<8, 8, 8>; static constexpr int threads = 128; };
-template <> struct Plan<1024> { using two = Radices<16, 8, 8>; using one = Radices<16, 8, 8>; static constexpr int threads = 256; };
+// Plans: for each size N, a few variants V of the radix list used for two
+// concurrent transforms (the pass kernels; `two`) and for a single transform
+// (`one`), with the CTA width they run on.  Wide radices keep the FP64
+// instruction count low; narrow ones and wider CTAs keep more warps in
+// flight.  A stage with more butterflies than threads gives each thread
+// several.  Variant 0 is the default; the autotuner (da_autotune) times the
+// variants of a grid on the context's own batch and keeps the fastest.  The
+// allocation-free control map uses variant 0.
+template <int N, int V = 0> struct Plan;
+template <> struct Plan<16, 0> { using two = Radices<4, 4>; using one = Radices<4, 4>; static constexpr int threads = 32; };
+template <> struct Plan<32, 0> { using two = Radices<4, 8>; using one = Radices<4, 8>; static constexpr int threads = 32; };
+template <> struct Plan<64, 0> { using two = Radices<4, 4, 4>; using one = Radices<4, 4, 4>; static constexpr int threads = 32; };
+template <> struct Plan<64, 1> { using two = Radices<8, 8>; using one = Radices<8, 8>; static constexpr int threads = 32; };
+template <> struct Plan<128, 0> { using two = Radices<4, 4, 8>; using one = Radices<4, 4, 8>; static constexpr int threads = 64; };
+template <> struct Plan<128, 1> { using two = Radices<8, 4, 4>; using one = Radices<8, 4, 4>; static constexpr int threads = 64; };
+template <> struct Plan<128, 2> { using two = Radices<4, 4, 8>; using one = Radices<4, 4, 8>; static constexpr int threads = 32; };
+template <> struct Plan<256, 0> { using two = Radices<4, 4, 4, 4>; using one = Radices<4, 4, 4, 4>; static constexpr int threads = 128; };
+template <> struct Plan<256, 1> { using two = Radices<8, 8, 4>; using one = Radices<8, 8, 4>; static constexpr int threads = 64; };
+template <> struct Plan<256, 2> { using two = Radices<4, 4, 4, 4>; using one = Radices<4, 4, 4, 4>; static constexpr int threads = 64; };
+template <> struct Plan<512, 0> { using two = Radices<8, 8, 8>; using one = Radices<8, 8, 8>; static constexpr int threads = 128; };
+template <> struct Plan<512, 1> { using two = Radices<8, 4, 4, 4>; using one = Radices<8, 4, 4, 4>; static constexpr int threads = 256; };
+template <> struct Plan<512, 2> { using two = Radices<8, 8, 8>; using one = Radices<8, 8, 8>; static constexpr int threads = 64; };
+template <> struct Plan<1024, 0> { using two = Radices<16, 8, 8>; using one = Radices<16, 8, 8>; static constexpr int threads = 256; };
+template <> struct Plan<1024, 1> { using two = Radices<16, 4, 4, 4>; using one = Radices<16, 4, 4, 4>; static constexpr int threads = 256; };
+template <> struct Plan<1024, 2> { using two = Radices<8, 8, 4, 4>; using one = Radices<8, 8, 4, 4>; static constexpr int threads = 256; };
 
-template <int N>
+// Number of plan variants of each size (the instantiations in inst_n*.cu).
+constexpr int plan_count(int n) {
+  return n == 64 ? 2 : (n == 128 || n == 256 || n == 512 || n == 1024) ? 3 : 1;
+}
+
+template <int N, int V = 0>
 struct PlanInfo {
-  static constexpr int THREADS = Plan<N>::threads;
+  static constexpr int THREADS = Plan<N, V>::threads;
 };
 
 // One in-place Stockham stage on F sequences of N points stored back to back
@@ -247,9 +264,9 @@ template <int L, int R, int... Rs> struct FoldSize<L, Radices<R, Rs...>> {
   static constexpr int value = (L > 1 ? FoldSlots<R>::value * L : 0) + FoldSize<L * R, Radices<Rs...>>::value;
 };
 
-template <int N>
+template <int N, int V = 0>
 struct FoldInfo {
-  static constexpr int DOUBLES = FoldSize<1, typename Plan<N>::two>::value;
+  static constexpr int DOUBLES = FoldSize<1, typename Plan<N, V>::two>::value;
   // padded to whole double2 so that the sequences after it stay aligned
   static constexpr int PADDED = (DOUBLES + 1) / 2 * 2;
 };
@@ -311,9 +328,9 @@ __device__ __forceinline__ void dft8_folded(double2* a, const double* T, int k, 
 }
 
 // One in-place Stockham stage with folded twiddles (T: this stage's table).
-template <int N, int R, int S, int F, int L>
+template <int N, int V, int R, int S, int F, int L>
 __device__ __forceinline__ void stockham_stage_folded(double2* buf, const double* __restrict__ T) {
-  constexpr int NB = N / R, Th = PlanInfo<N>::THREADS, TOT = F * NB, J = (TOT + Th - 1) / Th;
+  constexpr int NB = N / R, Th = PlanInfo<N, V>::THREADS, TOT = F * NB, J = (TOT + Th - 1) / Th;
   double2 a[J][R];
   int base[J], dst[J];
 #pragma unroll
@@ -350,25 +367,26 @@ __device__ __forceinline__ void stockham_stage_folded(double2* buf, const double
   __syncthreads();
 }
 
-template <int N, int S, int F, int L>
+template <int N, int V, int S, int F, int L>
 __device__ __forceinline__ void run_stages_folded(double2*, const double*, Radices<>) {}
 
-template <int N, int S, int F, int L, int R, int... Rs>
+template <int N, int V, int S, int F, int L, int R, int... Rs>
 __device__ __forceinline__ void run_stages_folded(double2* buf, const double* T, Radices<R, Rs...>) {
-  stockham_stage_folded<N, R, S, F, L>(buf, T);
-  run_stages_folded<N, S, F, L * R>(buf, T + (L > 1 ? FoldSlots<R>::value * L : 0), Radices<Rs...>{});
+  stockham_stage_folded<N, V, R, S, F, L>(buf, T);
+  run_stages_folded<N, V, S, F, L * R>(buf, T + (L > 1 ? FoldSlots<R>::value * L : 0), Radices<Rs...>{});
 }
 
 // Transform, in place, F (1 or 2) sequences of N points stored back to back
-// in buf, with the folded table of Plan<N>::two (both plans of a size are
-// the same list of radices) in shared memory.  Same contract as fft_batch.
-template <int N, int S, int F>
+// in buf, with the folded table of Plan<N, V>::two (both lists of a plan
+// are the same radices) in shared memory.  Same contract as fft_batch, on a
+// CTA of PlanInfo<N, V>::THREADS threads.
+template <int N, int V, int S, int F>
 __device__ __forceinline__ void fft_folded(double2* buf, const double* T) {
   static_assert(F == 1 || F == 2, "batches of one or two transforms");
-  run_stages_folded<N, S, F, 1>(buf, T, typename Plan<N>::two{});
+  run_stages_folded<N, V, S, F, 1>(buf, T, typename Plan<N, V>::two{});
 }
 
-// Host side: fill the folded table of Plan<N>::two (FoldInfo<N>::DOUBLES
+// Host side: fill the folded table of Plan<N, V>::two (FoldInfo<N, V>::DOUBLES
 // entries) for S = -1.
 template <int L>
 inline void fold_fill(double*, int, Radices<>) {}
@@ -398,9 +416,9 @@ inline void fold_fill(double* out, int n, Radices<R, Rs...>) {
   fold_fill<L * R>(out, n, Radices<Rs...>{});
 }
 
-template <int N>
+template <int N, int V>
 inline void fold_table(double* out) {
-  fold_fill<1>(out, N, typename Plan<N>::two{});
+  fold_fill<1>(out, N, typename Plan<N, V>::two{});
 }
 
 // Transform, in place, F (1 or 2) sequences of N points stored back to back

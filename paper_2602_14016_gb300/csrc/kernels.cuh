@@ -93,18 +93,18 @@ struct Dev {
   double dt2, dt3, dt6;                      // dt/2, dt/3, dt/6
 };
 
-template <int N>
+template <int N, int V = 0>
 struct Geo {
   static constexpr int K = (N - 1) / 3;
   static constexpr int Kc = K + 1;
   static constexpr int Kr = 2 * K + 1;
   static constexpr int NH = N / 2 + 1;
   // threads: two transforms at a time (fft.cuh)
-  static constexpr int THREADS = PlanInfo<N>::THREADS;
+  static constexpr int THREADS = PlanInfo<N, V>::THREADS;
   // shared memory: folded twiddle table + one buffer of two sequences +
   // probe sums
   static constexpr int PMAX = 64;
-  static constexpr size_t SMEM = sizeof(double) * FoldInfo<N>::PADDED + sizeof(double2) * (2 * N + 2 * PMAX);
+  static constexpr size_t SMEM = sizeof(double) * FoldInfo<N, V>::PADDED + sizeof(double2) * (2 * N + 2 * PMAX);
   // column passes load their epilogue inputs before the transforms (about
   // 60 more registers a thread) where a CTA is at most 128 threads
   static constexpr bool PREFETCH = THREADS <= 128;
@@ -112,9 +112,9 @@ struct Geo {
 
 __device__ __forceinline__ int ky_of_row(int r, int K) { return r <= K ? r : r - (2 * K + 1); }
 
-template <int N>
+template <int N, int V = 0>
 __device__ __forceinline__ void load_fold(double* T, const double* __restrict__ g) {
-  for (int i = threadIdx.x; i < FoldInfo<N>::DOUBLES; i += blockDim.x) T[i] = g[i];
+  for (int i = threadIdx.x; i < FoldInfo<N, V>::DOUBLES; i += blockDim.x) T[i] = g[i];
 }
 
 // Observation slot of step k, or -1.
@@ -127,9 +127,9 @@ __device__ __forceinline__ int obs_slot(const Dev& d, int k) {
 // Full-length sequence whose inverse transform is a + i b, for two real rows
 // a, b given by their mixed half spectra A, B (kx = 0..K): Z(kx) = A + iB,
 // Z(-kx) = conj(A) + i conj(B); the DC bin keeps real parts only.
-template <int N>
+template <int N, int V = 0>
 __device__ __forceinline__ double2 pack_pair(const double2* __restrict__ A, const double2* __restrict__ Bv, int kx) {
-  constexpr int K = Geo<N>::K;
+  constexpr int K = Geo<N, V>::K;
   if (kx == 0) return make_double2(A[0].x, Bv[0].x);
   if (kx <= K) {
     const double2 p = A[kx], q = Bv[kx];
@@ -170,7 +170,7 @@ __device__ __forceinline__ void pack_rows(double2* seq, const double2* __restric
 
 // The two half spectra packed in a forward transform Z of a + i b:
 // A(k) = (Z(k) + conj Z(-k))/2, B(k) = -i (Z(k) - conj Z(-k))/2.
-template <int N>
+template <int N, int V = 0>
 __device__ __forceinline__ void unpack_pair(const double2* Z, int kx, double2& A, double2& Bv) {
   const double2 zk = Z[kx], zm = Z[(N - kx) & (N - 1)];
   const double sx = zk.x + zm.x, sy = zk.y - zm.y;
@@ -181,7 +181,7 @@ __device__ __forceinline__ void unpack_pair(const double2* Z, int kx, double2& A
 
 // Twice the two half spectra (no 1/2): the pass kernels fold the 1/2 into
 // the per-mode symbols of the column pass that consumes them.
-template <int N>
+template <int N, int V = 0>
 __device__ __forceinline__ void unpack_pair2(const double2* Z, int kx, double2& A, double2& Bv) {
   const double2 zk = Z[kx], zm = Z[(N - kx) & (N - 1)];
   A = make_double2(zk.x + zm.x, zk.y - zm.y);
@@ -194,19 +194,19 @@ __device__ __forceinline__ void unpack_pair2(const double2* Z, int kx, double2& 
 
 // Real rows in[b][y][x] -> mixed half rows Mn[b][y][kx], kx <= K (forward,
 // unnormalised), two rows per complex transform.  grid (N/2, B).
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_r2c_rows(Dev d, const double* __restrict__ in) {
-  using G = Geo<N>;
+template <int N, int V = 0>
+__global__ void __launch_bounds__(Geo<N, V>::THREADS) k_r2c_rows(Dev d, const double* __restrict__ in) {
+  using G = Geo<N, V>;
   extern __shared__ double2 sm[];
   double* T = reinterpret_cast<double*>(sm);
-  double2* a = sm + FoldInfo<N>::PADDED / 2;
+  double2* a = sm + FoldInfo<N, V>::PADDED / 2;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
-  load_fold<N>(T, d.fold);
+  load_fold<N, V>(T, d.fold);
   const double* r0 = in + ((size_t)bm * N + y0) * N;
   #pragma unroll
   for (int x = threadIdx.x; x < N; x += G::THREADS) a[x] = make_double2(r0[x], r0[N + x]);
   __syncthreads();
-  fft_folded<N, -1, 1>(a, T);
+  fft_folded<N, V, -1, 1>(a, T);
   double2* M = d.Mn + ((size_t)bm * 2 * N + y0) * G::Kc;
   #pragma unroll
   for (int kx = threadIdx.x; kx < G::Kc; kx += G::THREADS) {
@@ -219,18 +219,18 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_r2c_rows(Dev d, const doubl
 
 // Mixed half rows Mn[b][y][kx] -> real rows out[b][y][x] (the inverse along
 // x; the 1/N^2 is already in Mn), two rows per complex transform.
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_c2r_rows(Dev d, double* __restrict__ out) {
-  using G = Geo<N>;
+template <int N, int V = 0>
+__global__ void __launch_bounds__(Geo<N, V>::THREADS) k_c2r_rows(Dev d, double* __restrict__ out) {
+  using G = Geo<N, V>;
   extern __shared__ double2 sm[];
   double* T = reinterpret_cast<double*>(sm);
-  double2* a = sm + FoldInfo<N>::PADDED / 2;
+  double2* a = sm + FoldInfo<N, V>::PADDED / 2;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
-  load_fold<N>(T, d.fold);
+  load_fold<N, V>(T, d.fold);
   const double2* M = d.Mn + ((size_t)bm * 2 * N + y0) * G::Kc;
   pack_rows<N, G::THREADS>(a, M, M + G::Kc);
   __syncthreads();
-  fft_folded<N, +1, 1>(a, T);
+  fft_folded<N, V, +1, 1>(a, T);
   double* r0 = out + ((size_t)bm * N + y0) * N;
   #pragma unroll
   for (int x = threadIdx.x; x < N; x += G::THREADS) {
@@ -241,14 +241,14 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_c2r_rows(Dev d, double* __r
 
 // Compact spectrum src[b] times a multiplier (and 1/N^2), transformed along
 // y -> mixed Mn[b] (first field).  grid (Kc, B).
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_spec_to_mixed(Dev d, const double2* __restrict__ src, int mode) {
-  using G = Geo<N>;
+template <int N, int V = 0>
+__global__ void __launch_bounds__(Geo<N, V>::THREADS) k_spec_to_mixed(Dev d, const double2* __restrict__ src, int mode) {
+  using G = Geo<N, V>;
   extern __shared__ double2 sm[];
   double* T = reinterpret_cast<double*>(sm);
-  double2* a = sm + FoldInfo<N>::PADDED / 2;
+  double2* a = sm + FoldInfo<N, V>::PADDED / 2;
   const int kx = blockIdx.x, bm = blockIdx.y;
-  load_fold<N>(T, d.fold);
+  load_fold<N, V>(T, d.fold);
   const double s = 1.0 / ((double)N * N);
   #pragma unroll
   for (int q = threadIdx.x; q < N; q += G::THREADS) {
@@ -268,16 +268,16 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_spec_to_mixed(Dev d, const 
     a[q] = v;
   }
   __syncthreads();
-  fft_folded<N, +1, 1>(a, T);
+  fft_folded<N, V, +1, 1>(a, T);
   double2* M = d.Mn + (size_t)bm * 2 * N * G::Kc + kx;
   #pragma unroll
   for (int y = threadIdx.x; y < N; y += G::THREADS) M[(size_t)y * G::Kc] = a[y];
 }
 
 // Compact <-> half-spectrum copies.  grid (ceil(N*NH/256), B), block 256.
-template <int N>
+template <int N, int V = 0>
 __global__ void k_compact_to_half(const double2* __restrict__ src, double2* __restrict__ out) {
-  using G = Geo<N>;
+  using G = Geo<N, V>;
   const int bm = blockIdx.y;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * G::NH; i += gridDim.x * blockDim.x) {
     const int q = i / G::NH, p = i - q * G::NH;
@@ -291,9 +291,9 @@ __global__ void k_compact_to_half(const double2* __restrict__ src, double2* __re
   }
 }
 
-template <int N>
+template <int N, int V = 0>
 __global__ void k_half_to_compact(const double2* __restrict__ in, double2* __restrict__ dst) {
-  using G = Geo<N>;
+  using G = Geo<N, V>;
   const int bm = blockIdx.y;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G::Kr * G::Kc; i += gridDim.x * blockDim.x) {
     const int r = i / G::Kc, kx = i - r * G::Kc;
@@ -308,7 +308,7 @@ __global__ void k_half_to_compact(const double2* __restrict__ in, double2* __res
 
 // Writes the two column values u = i ky/k^2 Yv, v = -i kx/k^2 Yv (scaled by
 // 1/N^2; f = symF entry of the mode) into position q of seq[0..1][N].
-template <int N>
+template <int N, int V = 0>
 __device__ __forceinline__ void put_stage_columns(double2* seq, int q, const Sym4& f, double2 Yv) {
   seq[q] = make_double2(-f.a * Yv.y, f.a * Yv.x);      // u:  i ky / k^2
   seq[N + q] = make_double2(f.b * Yv.y, -f.b * Yv.x);  // v: -i kx / k^2
@@ -317,16 +317,16 @@ __device__ __forceinline__ void put_stage_columns(double2* seq, int q, const Sym
 // Writes the two column values of the adjoint fields of an adjoint stage
 // value kb: 2a = 2 d_xy kb = -2 kx ky kb and b = (d_xx - d_yy) kb =
 // (ky^2 - kx^2) kb, scaled by 1/N^2 (g = symA entry of the mode), at q.
-template <int N>
+template <int N, int V = 0>
 __device__ __forceinline__ void put_adjoint_columns(double2* seq, int q, const Sym4& g, double2 kb) {
   seq[q] = cscale(kb, g.c);
   seq[N + q] = cscale(kb, g.d);
 }
 
 // Zeroes the positions outside the retained set in `nseq` sequences.
-template <int N>
+template <int N, int V = 0>
 __device__ __forceinline__ void zero_outside(double2* seq, int nseq) {
-  constexpr int K = Geo<N>::K, GAP = N - 2 * K - 1;
+  constexpr int K = Geo<N, V>::K, GAP = N - 2 * K - 1;
   for (int u = threadIdx.x; u < nseq * GAP; u += blockDim.x) {
     const int f = u / GAP, q = K + 1 + (u - f * GAP);
     seq[f * N + q] = make_double2(0.0, 0.0);
@@ -334,9 +334,9 @@ __device__ __forceinline__ void zero_outside(double2* seq, int nseq) {
 }
 
 // The two transformed columns of seq -> column kx of both fields of Mx[bm].
-template <int N>
+template <int N, int V = 0>
 __device__ __forceinline__ void store_mixed2(const Dev& d, const double2* z, int bm, int kx) {
-  using G = Geo<N>;
+  using G = Geo<N, V>;
   double2* M = d.Mx + (size_t)bm * 2 * N * G::Kc + kx;
 #pragma unroll
   for (int t = 0; t < (2 * N + G::THREADS - 1) / G::THREADS; ++t) {
@@ -360,20 +360,20 @@ __device__ __forceinline__ void load_column(double2* seq, const double2* __restr
 // Both rows y0, y0+1 of the two fields of a mixed buffer, packed for the
 // inverse transform along x: sequence rr holds row y0+rr of (field 0,
 // field 1) as field0 + i field1.
-template <int N>
+template <int N, int V = 0>
 __device__ __forceinline__ void pack_field_pairs(double2* a, const double2* __restrict__ M, int y0) {
-  constexpr int Kc = Geo<N>::Kc;
+  constexpr int Kc = Geo<N, V>::Kc;
 #pragma unroll
   for (int rr = 0; rr < 2; ++rr)
-    pack_rows<N, Geo<N>::THREADS>(a + rr * N, M + (size_t)(y0 + rr) * Kc, M + ((size_t)N + y0 + rr) * Kc);
+    pack_rows<N, Geo<N, V>::THREADS>(a + rr * N, M + (size_t)(y0 + rr) * Kc, M + ((size_t)N + y0 + rr) * Kc);
 }
 
 // Forward transforms along x of rows y0, y0+1 of two real fields, packed as
 // seq f = (field f row y0) + i (field f row y0+1) -> twice the rows of both
 // fields of the mixed buffer O (kx <= K).
-template <int N>
+template <int N, int V = 0>
 __device__ __forceinline__ void unpack_field_rows(const double2* a, double2* __restrict__ O, int y0) {
-  using G = Geo<N>;
+  using G = Geo<N, V>;
 #pragma unroll
   for (int t = 0; t < (2 * G::Kc + G::THREADS - 1) / G::THREADS; ++t) {
     const int u = threadIdx.x + t * G::THREADS;
@@ -390,18 +390,18 @@ __device__ __forceinline__ void unpack_field_rows(const double2* a, double2* __r
 // s_hat = forward transform along y of the mixed rows in Mn; w0 = mult s_hat
 // into W (and Y); then, unless F_NO_NEXT, the inverse column transforms of
 // u and v of stage 1.  grid (Kc, B).
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_ctrl_cols(Dev d, int flags) {
-  using G = Geo<N>;
+template <int N, int V = 0>
+__global__ void __launch_bounds__(Geo<N, V>::THREADS) k_ctrl_cols(Dev d, int flags) {
+  using G = Geo<N, V>;
   extern __shared__ double2 sm[];
   double* T = reinterpret_cast<double*>(sm);
-  double2* a = sm + FoldInfo<N>::PADDED / 2;
+  double2* a = sm + FoldInfo<N, V>::PADDED / 2;
   const int kx = blockIdx.x, bm = blockIdx.y;
-  load_fold<N>(T, d.fold);
+  load_fold<N, V>(T, d.fold);
   const double2* M = d.Mn + (size_t)bm * 2 * N * G::Kc + kx;
   load_column<N, G::THREADS, 1>(a, M);
   __syncthreads();
-  fft_folded<N, -1, 1>(a, T);
+  fft_folded<N, V, -1, 1>(a, T);
   // each retained position is read and rewritten by one thread only
   #pragma unroll
   for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
@@ -415,20 +415,20 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_ctrl_cols(Dev d, int flags)
   if (flags & F_NO_NEXT) return;
   zero_outside<N>(a, 2);
   __syncthreads();
-  fft_folded<N, +1, 2>(a, T);
-  store_mixed2<N>(d, a, bm, kx);
+  fft_folded<N, V, +1, 2>(a, T);
+  store_mixed2<N, V>(d, a, bm, kx);
 }
 
 // Restart from the compact state in W (a checkpoint): Y = W and the inverse
 // column transforms of u and v of stage 1.  grid (Kc, B).
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_state_cols(Dev d) {
-  using G = Geo<N>;
+template <int N, int V = 0>
+__global__ void __launch_bounds__(Geo<N, V>::THREADS) k_state_cols(Dev d) {
+  using G = Geo<N, V>;
   extern __shared__ double2 sm[];
   double* T = reinterpret_cast<double*>(sm);
-  double2* a = sm + FoldInfo<N>::PADDED / 2;
+  double2* a = sm + FoldInfo<N, V>::PADDED / 2;
   const int kx = blockIdx.x, bm = blockIdx.y;
-  load_fold<N>(T, d.fold);
+  load_fold<N, V>(T, d.fold);
   zero_outside<N>(a, 2);
   #pragma unroll
   for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
@@ -439,8 +439,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_state_cols(Dev d) {
     put_stage_columns<N>(a, ky & (N - 1), d.symF[kx * G::Kr + rr], w);
   }
   __syncthreads();
-  fft_folded<N, +1, 2>(a, T);
-  store_mixed2<N>(d, a, bm, kx);
+  fft_folded<N, V, +1, 2>(a, T);
+  store_mixed2<N, V>(d, a, bm, kx);
 }
 
 // ---------------------------------------------------------------------------
@@ -450,17 +450,17 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_state_cols(Dev d) {
 // Row pass of stage `stage` (1..4) of step n: u, v of rows y0, y0+1; the
 // stage-field store and probe gather; the products u v and v^2 - u^2 and
 // their forward transforms along x into Mn.  grid (N/2, B).
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_rows(Dev d, int n, int stage, int flags) {
-  using G = Geo<N>;
+template <int N, int V = 0>
+__global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_rows(Dev d, int n, int stage, int flags) {
+  using G = Geo<N, V>;
   extern __shared__ double2 sm[];
   double* T = reinterpret_cast<double*>(sm);
-  double2* a = sm + FoldInfo<N>::PADDED / 2;
+  double2* a = sm + FoldInfo<N, V>::PADDED / 2;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
-  load_fold<N>(T, d.fold);
-  pack_field_pairs<N>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
+  load_fold<N, V>(T, d.fold);
+  pack_field_pairs<N, V>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
   __syncthreads();
-  fft_folded<N, +1, 2>(a, T);
+  fft_folded<N, V, +1, 2>(a, T);
   const int st = N / d.px;
   const int slot = (flags & (F_OBS | F_OBS_ONLY)) ? obs_slot(d, n) : -1;
   double* trj = (flags & F_STORE)
@@ -494,8 +494,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_rows(Dev d, int n, int 
   }
   if (flags & F_OBS_ONLY) return;
   __syncthreads();
-  fft_folded<N, -1, 2>(a, T);
-  unpack_field_rows<N>(a, d.Mn + (size_t)bm * 2 * N * G::Kc, y0);
+  fft_folded<N, V, -1, 2>(a, T);
+  unpack_field_rows<N, V>(a, d.Mn + (size_t)bm * 2 * N * G::Kc, y0);
 }
 
 // Column pass of stage `stage`: the advection term
@@ -503,14 +503,14 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_rows(Dev d, int n, int 
 // k_j = -n_hat - nu k^2 y_j + f_hat, the RK4 update, and the inverse column
 // transforms of u and v of the next stage state.  Acc holds k1 + 2 k2 +
 // 2 k3 (+ k4).  grid (Kc, B).
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, int flags) {
-  using G = Geo<N>;
+template <int N, int V = 0>
+__global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_cols(Dev d, int stage, int flags) {
+  using G = Geo<N, V>;
   extern __shared__ double2 sm[];
   double* T = reinterpret_cast<double*>(sm);
-  double2* a = sm + FoldInfo<N>::PADDED / 2;
+  double2* a = sm + FoldInfo<N, V>::PADDED / 2;
   const int kx = blockIdx.x, bm = blockIdx.y;
-  load_fold<N>(T, d.fold);
+  load_fold<N, V>(T, d.fold);
   load_column<N, G::THREADS, 2>(a, d.Mn + (size_t)bm * 2 * N * G::Kc + kx);
   // the epilogue's inputs for this thread's modes; where registers allow
   // (G::PREFETCH), loaded now so that their latency hides behind the
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, 
     for (int t = 0; t < MT; ++t) load_inputs(t);
   }
   __syncthreads();
-  fft_folded<N, -1, 2>(a, T);
+  fft_folded<N, V, -1, 2>(a, T);
   const double dt = d.dt;
   const double fval = -d.amp * d.nf * (double)N * N / 2.0;
   // each retained position is read and rewritten (both sequences) by one
@@ -574,8 +574,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_fwd_cols(Dev d, int stage, 
   if (flags & F_NO_NEXT) return;
   zero_outside<N>(a, 2);
   __syncthreads();
-  fft_folded<N, +1, 2>(a, T);
-  store_mixed2<N>(d, a, bm, kx);
+  fft_folded<N, V, +1, 2>(a, T);
+  store_mixed2<N, V>(d, a, bm, kx);
 }
 
 // r = model observations - data and J = 1/2 sum r^2 per member, in a fixed
@@ -651,14 +651,14 @@ __device__ __forceinline__ double2 probe_source(const Dev& d, int kx, int ky, co
 // with INIT_RESUME, KB as it stands (after a checkpoint recompute).  Then
 // the inverse column transforms of the adjoint fields a, b of KB into Mx.
 // grid (Kc, B).
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_init(Dev d, int mode) {
-  using G = Geo<N>;
+template <int N, int V = 0>
+__global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_init(Dev d, int mode) {
+  using G = Geo<N, V>;
   extern __shared__ double2 sm[];
   double* T = reinterpret_cast<double*>(sm);
-  double2 *a = sm + FoldInfo<N>::PADDED / 2, *Tu = a + 2 * N, *Tv = Tu + G::PMAX;
+  double2 *a = sm + FoldInfo<N, V>::PADDED / 2, *Tu = a + 2 * N, *Tv = Tu + G::PMAX;
   const int kx = blockIdx.x, bm = blockIdx.y;
-  load_fold<N>(T, d.fold);
+  load_fold<N, V>(T, d.fold);
   const bool resume = (mode & INIT_RESUME) != 0;
   const int slot = (!resume && (mode & INIT_SRC)) ? obs_slot(d, d.nsteps) : -1;
   if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
@@ -681,25 +681,25 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_init(Dev d, int mode) {
     put_adjoint_columns<N>(a, ky & (N - 1), d.symA[kx * G::Kr + rr], kb);
   }
   __syncthreads();
-  fft_folded<N, +1, 2>(a, T);
-  store_mixed2<N>(d, a, bm, kx);
+  fft_folded<N, V, +1, 2>(a, T);
+  store_mixed2<N, V>(d, a, bm, kx);
 }
 
 // Adjoint row pass of stage `stage` of step n: 2a, b of rows y0, y0+1
 // (inverse transforms along x), rho_u and rho_v with the stored u, v, and
 // their forward transforms along x into Mn (twice, as in the forward row
 // pass).  grid (N/2, B).
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_rows(Dev d, int n, int stage) {
-  using G = Geo<N>;
+template <int N, int V = 0>
+__global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_rows(Dev d, int n, int stage) {
+  using G = Geo<N, V>;
   extern __shared__ double2 sm[];
   double* T = reinterpret_cast<double*>(sm);
-  double2* a = sm + FoldInfo<N>::PADDED / 2;
+  double2* a = sm + FoldInfo<N, V>::PADDED / 2;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
-  load_fold<N>(T, d.fold);
-  pack_field_pairs<N>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
+  load_fold<N, V>(T, d.fold);
+  pack_field_pairs<N, V>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
   __syncthreads();
-  fft_folded<N, +1, 2>(a, T);
+  fft_folded<N, V, +1, 2>(a, T);
   const double* trj = d.traj + (((size_t)bm * d.traj_steps + (n - d.seg0)) * 4 + (stage - 1)) * 2 * (size_t)N * N;
   // one thread per column x reads (a, b) of both rows, then writes
   // rho_u and rho_v of both rows at x
@@ -718,8 +718,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_rows(Dev d, int n, int 
     a[N + x] = make_double2(rv[0], rv[1]);
   }
   __syncthreads();
-  fft_folded<N, -1, 2>(a, T);
-  unpack_field_rows<N>(a, d.Mn + (size_t)bm * 2 * N * G::Kc, y0);
+  fft_folded<N, V, -1, 2>(a, T);
+  unpack_field_rows<N, V>(a, d.Mn + (size_t)bm * 2 * N * G::Kc, y0);
 }
 
 // Adjoint column pass of stage `stage` of step n:
@@ -727,14 +727,14 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_rows(Dev d, int n, int 
 // the transposed RK4 combination, the observation source at step n (on
 // stage 1), and the inverse column transforms of a, b of the next kbar.
 // grid (Kc, B).
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int stage, int flags) {
-  using G = Geo<N>;
+template <int N, int V = 0>
+__global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_cols(Dev d, int n, int stage, int flags) {
+  using G = Geo<N, V>;
   extern __shared__ double2 sm[];
   double* T = reinterpret_cast<double*>(sm);
-  double2 *a = sm + FoldInfo<N>::PADDED / 2, *Tu = a + 2 * N, *Tv = Tu + G::PMAX;
+  double2 *a = sm + FoldInfo<N, V>::PADDED / 2, *Tu = a + 2 * N, *Tv = Tu + G::PMAX;
   const int kx = blockIdx.x, bm = blockIdx.y;
-  load_fold<N>(T, d.fold);
+  load_fold<N, V>(T, d.fold);
   load_column<N, G::THREADS, 2>(a, d.Mn + (size_t)bm * 2 * N * G::Kc + kx);
   // the epilogue's inputs for this thread's modes (before the column
   // transforms where registers allow, as in k_fwd_cols)
@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int 
   const int slot = (flags & F_SRC) ? obs_slot(d, n) : -1;
   if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
   __syncthreads();
-  fft_folded<N, -1, 2>(a, T);
+  fft_folded<N, V, -1, 2>(a, T);
   const double dt = d.dt;
   // each retained position is read and rewritten (both sequences) by one
   // thread only
@@ -802,16 +802,16 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_adj_cols(Dev d, int n, int 
   if (flags & F_FINAL) return;
   zero_outside<N>(a, 2);
   __syncthreads();
-  fft_folded<N, +1, 2>(a, T);
-  store_mixed2<N>(d, a, bm, kx);
+  fft_folded<N, V, +1, 2>(a, T);
+  store_mixed2<N, V>(d, a, bm, kx);
 }
 
 // Control multipliers m(k) = |k| W(k)^{1/2} on the retained set (0 at k = 0),
 // per member.  grid (ceil(Kr*Kc/256), B), block 256.
-template <int N>
+template <int N, int V = 0>
 __global__ void k_make_mult(double* __restrict__ mult, const int* __restrict__ kind, const double* __restrict__ param,
                             const double* __restrict__ table, double nu) {
-  using G = Geo<N>;
+  using G = Geo<N, V>;
   const int bm = blockIdx.y;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G::Kr * G::Kc; i += gridDim.x * blockDim.x) {
     const int r = i / G::Kc, kx = i - r * G::Kc;

@@ -9,6 +9,8 @@ namespace da {
 
 struct Ops {
   int n, K, Kc, Kr;
+  int variant;                      // plan variant (fft.cuh)
+  int threads;                      // CTA width of the pass kernels
   int fold_doubles;                 // entries of the folded twiddle table
   void (*fold_table)(double* out);  // fills it on the host
   cudaError_t (*setup)();
@@ -28,23 +30,34 @@ struct Ops {
                     cudaStream_t);
 };
 
-const Ops* ops_n16();
-const Ops* ops_n32();
-const Ops* ops_n64();
-const Ops* ops_n128();
-const Ops* ops_n256();
-const Ops* ops_n512();
-const Ops* ops_n1024();
+const Ops* ops_n16_v0();
+const Ops* ops_n32_v0();
+const Ops* ops_n64_v0();
+const Ops* ops_n64_v1();
+const Ops* ops_n128_v0();
+const Ops* ops_n128_v1();
+const Ops* ops_n128_v2();
+const Ops* ops_n256_v0();
+const Ops* ops_n256_v1();
+const Ops* ops_n256_v2();
+const Ops* ops_n512_v0();
+const Ops* ops_n512_v1();
+const Ops* ops_n512_v2();
+const Ops* ops_n1024_v0();
+const Ops* ops_n1024_v1();
+const Ops* ops_n1024_v2();
 
-inline const Ops* ops_for(int n) {
+// Launchers of plan variant v of size n (v < plan_count(n)), or nullptr.
+inline const Ops* ops_for(int n, int v = 0) {
+  if (v < 0 || v >= plan_count(n)) return nullptr;
   switch (n) {
-    case 16: return ops_n16();
-    case 32: return ops_n32();
-    case 64: return ops_n64();
-    case 128: return ops_n128();
-    case 256: return ops_n256();
-    case 512: return ops_n512();
-    case 1024: return ops_n1024();
+    case 16: return ops_n16_v0();
+    case 32: return ops_n32_v0();
+    case 64: return v == 0 ? ops_n64_v0() : ops_n64_v1();
+    case 128: return v == 0 ? ops_n128_v0() : v == 1 ? ops_n128_v1() : ops_n128_v2();
+    case 256: return v == 0 ? ops_n256_v0() : v == 1 ? ops_n256_v1() : ops_n256_v2();
+    case 512: return v == 0 ? ops_n512_v0() : v == 1 ? ops_n512_v1() : ops_n512_v2();
+    case 1024: return v == 0 ? ops_n1024_v0() : v == 1 ? ops_n1024_v1() : ops_n1024_v2();
     default: return nullptr;
   }
 }

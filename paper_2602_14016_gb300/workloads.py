@@ -73,6 +73,7 @@ def ensemble_statistics(api, torch, groups, nsteps=1000, save_every=10, ckpt_eve
         cfg = api.Config(n=n, nsteps=nsteps, dt=g["dt"], nu=g["nu"], px=1, every=nsteps,
                          kernels=[api.KernelSpec("identity", 0.0)] * B, ckpt_every=ckpt_every)
         ctx = api.Context(cfg)
+        g["fft_plan"], g["plan_ms_per_step"] = ctx.autotune(4)  # the autotuner picks the plan per grid and batch
         w = torch.from_numpy(np.stack([synthetic.random_vorticity_hat(n, g["seed0"] + b) for b in range(B)]))
         s = ctx.control_from_omega(w.to(ctx.device))
         lamT = torch.from_numpy(np.stack([synthetic.unit_norm_terminal_hat(n, 10_000 + g["seed0"] + b)
