@@ -53,7 +53,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # (256^2, batch 7), from one ncu capture of the same launch configuration on
 # a 40-step window (per-launch data are the same for any window length);
 # valid only for the kernel sources they were taken from.
-TRAFFIC = {"src_hash": "103aa6fd6cc2260a", "adj_rows": 12299008, "adj_cols": 10526720, "fwd_rows": 4971264,
+TRAFFIC = {"src_hash": "951818d5e3817901", "adj_rows": 12299264, "adj_cols": 10526464, "fwd_rows": 4971520,
            "fwd_cols": 10492160}
 
 
@@ -492,7 +492,7 @@ def main():
     ap.add_argument("--ens-ckpt", type=int, default=25)
     ap.add_argument("--ag-n", type=int, default=512)
     ap.add_argument("--ag-steps", type=int, default=4000)
-    ap.add_argument("--ag-dirs", type=int, default=8)
+    ap.add_argument("--ag-dirs", type=int, default=20)
     ap.add_argument("--rates", type=float, nargs="+", default=[2.0, 10.0])
     ap.add_argument("--serve-jobs", type=int, default=16)
     ap.add_argument("--slots", type=int, default=4)
