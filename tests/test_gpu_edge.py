@@ -126,3 +126,32 @@ def test_single_probe_observed_only_at_t0(orc, api):
     Jg, gg = ctx.cost_grad(cu(guess[None]))
     assert abs(Jg.item() - J) <= 1e-12 * J
     assert rel(gg.cpu().numpy()[0], g) < 1e-8
+
+
+@pytest.mark.parametrize("n,kx,ky", [(64, 1, 2), (128, 3, -2), (256, 5, 0)])
+def test_single_taylor_green_mode_decays_by_the_rk4_factor(api, n, kx, ky):
+    """w = cos(kx x + ky y) is a steady Euler solution (u . grad w = 0, the
+    advection term of a single |k| shell vanishes), so RK4 multiplies its
+    coefficient by R(z) per step, z = -nu |k|^2 dt, and no other mode is
+    excited.  In the divergence form the two products cancel only in
+    (d_xx - d_yy)(u v) + d_xy (v^2 - u^2): this checks that cancellation."""
+    steps, dt, nu = 60, 1e-2, 2e-2
+    cfg = api.Config(n=n, nsteps=steps, dt=dt, nu=nu, px=8, every=steps, store=False)
+    ctx = api.Context(cfg)
+    w0 = np.zeros((n, n // 2 + 1), complex)
+    if kx == 0:
+        w0[ky % n, 0] = w0[-ky % n, 0] = n * n / 2
+    else:
+        w0[ky % n, kx] = n * n / 2
+    s = ctx.control_from_omega(cu(w0[None]))
+    wT, _ = ctx.forward(s)
+    z = -Fraction(nu) * (kx * kx + ky * ky) * Fraction(dt)
+    R = 1 + z + z * z / 2 + z**3 / 6 + z**4 / 24
+    amp = float(Fraction(n * n, 2) * R**steps)
+    w = wT.cpu().numpy()[0]
+    assert abs(w[ky % n, kx] - amp) <= 1e-13 * amp
+    w[ky % n, kx] = 0
+    if kx == 0:
+        assert abs(w[-ky % n, 0] - amp) <= 1e-13 * amp
+        w[-ky % n, 0] = 0
+    assert np.abs(w).max() <= 1e-13 * amp
