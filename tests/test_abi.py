@@ -78,3 +78,18 @@ def test_invalid_problems_are_rejected_on_the_host(lib, kw, frag):
     st, msg = _create(lib, **kw)
     assert st == N.DA_EINVAL
     assert frag in msg
+
+
+def test_plan_variant_queries_on_the_host(lib):
+    """Plan counts per supported size, 0 elsewhere; NULL contexts are rejected
+    before any device work."""
+    counts = {16: 1, 32: 1, 64: 2, 128: 3, 256: 3, 512: 3, 1024: 3}
+    for n, c in counts.items():
+        assert lib.da_plan_count(n) == c
+    for n in (0, 8, 48, 100, 2048):
+        assert lib.da_plan_count(n) == 0
+    assert lib.da_get_plan(None) == -1
+    assert lib.da_set_plan(None, 0) == 1  # DA_EINVAL
+    chosen = ctypes.c_int(-7)
+    assert lib.da_autotune(None, 4, ctypes.byref(chosen), None) == 1
+    assert chosen.value == -7
