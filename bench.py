@@ -70,6 +70,22 @@ def src_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def hbm_fraction(traffic, avg_ms):
+    """DRAM bandwidth the dominant kernel uses (measured bytes per launch over
+    its launch time) against the measured HBM copy peak: the %HBM view of a
+    kernel whose bound is the FP64 pipe."""
+    if traffic is None or not avg_ms:
+        return None
+    peak, src = 6800.0, "fallback"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, src = float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        pass
+    gbs = traffic / (avg_ms * 1e-3) / 1e9
+    return {"achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak, "peak_source": src}
+
+
 def fft_flops(n: int) -> float:
     """Nominal flops of one complex length-n FFT (5 n log2 n)."""
     return 5.0 * n * np.log2(n)
@@ -352,7 +368,8 @@ def run_gpu(args):
                      "flops_per_launch": pf, "avg_launch_ms": avg_ms, "launches_timed": dom_n,
                      "timed_in": "roofline pass of the same workload, direct launches, CUDA events per launch",
                      "roofline_pass_ms_per_step": roof_pass_ms,
-                     "class_ms_warmup": {k: v[0] for k, v in class_ms.items()}},
+                     "class_ms_warmup": {k: v[0] for k, v in class_ms.items()},
+                     "hbm": hbm_fraction(traffic, avg_ms)},
         "flops_per_gridpoint_step": flops_per_gridpoint_step(n),
         "achieved_gflops_step": value * flops_per_gridpoint_step(n) / 1e9,
         "cpu_baseline": cpu,
