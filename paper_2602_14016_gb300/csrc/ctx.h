@@ -1,0 +1,144 @@
+// ctx.h -- the context behind the C ABI of include/da.h and the host
+// helpers shared by the files that implement it (da_api.cu: creation,
+// forward, cost and gradient, adjoint variants; plans.cu: FFT plan variants
+// and the autotuner; lbfgs.cu: the optimiser).  Internal: nothing here is
+// part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/da.h"
+#include "ops.h"
+
+using da::Dev;
+using da::Ops;
+
+struct da_ctx {
+  int device = 0;
+  int n = 0, nsteps = 0, ckpt = 0, B = 1;
+  double dt = 0, nu = 0;
+  da_forcing force{};
+  da_obs_operator obs{};
+  int nt = 0, P = 0;
+  const Ops* ops = nullptr;
+  Dev dev{};
+  std::vector<void*> allocs;
+  unsigned long long bytes = 0;
+  unsigned long long launches = 0;
+  bool have_obs = false;
+  bool have_adj = false;
+  bool have_fwd = false;  // a stored forward (stage fields / checkpoints) is valid
+  int nckpt = 0;          // checkpoints held (ckpt > 0)
+  double2* ckpt_buf = nullptr;
+  double sobolev = 0.0;   // lambda of the regularisation term of Eq. (4)
+  // shell lists of the adjoint spectra (built on the first da_adjoint_spectra)
+  int nshell = 0;
+  int *shell_off = nullptr, *shell_mode = nullptr;
+  double *shell_wgt = nullptr, *shell_scratch = nullptr;
+  double2* w0 = nullptr;  // compact initial state kept for that term
+  std::string err;
+  // optimiser buffers (allocated on first da_assimilate)
+  double *x = nullptr, *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr, *S = nullptr, *Y = nullptr;
+  double *part = nullptr, *dots = nullptr, *scal = nullptr;
+  void** ptrs = nullptr;
+  int mem = 0;
+  // CUDA-graph replay of da_cost_grad
+  bool use_graph = false;
+  cudaGraphExec_t cg_exec = nullptr;
+  unsigned long long cg_launches = 0;  // kernel nodes in the captured graph
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  double *sbuf = nullptr, *gbuf = nullptr;
+  // event timing of one kernel class
+  int timed_class = 0;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+};
+
+// Message of the last failed da_create (no context to hold it).
+extern std::string g_create_error;
+
+#define DA_TRY_CUDA(ctx, call)                                                                    \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail((ctx), DA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+inline da_status fail(da_ctx* c, da_status s, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_create_error = msg;
+  return s;
+}
+
+inline da_status check_launch(da_ctx* c, unsigned long long nlaunch = 1) {
+  c->launches += nlaunch;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, DA_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return DA_OK;
+}
+
+// Brackets one launch of kernel class `cls` with events when that class is timed.
+struct Timed {
+  da_ctx* c;
+  bool on;
+  cudaStream_t st;
+  Timed(da_ctx* c_, int cls, cudaStream_t s) : c(c_), on(c_->timed_class == cls), st(s) {
+    if (!on) return;
+    if (c->ev_used + 2 > c->ev.size()) {
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+          on = false;
+          return;
+        }
+        c->ev.push_back(e);
+      }
+    }
+    cudaEventRecord(c->ev[c->ev_used], st);
+  }
+  ~Timed() {
+    if (!on) return;
+    cudaEventRecord(c->ev[c->ev_used + 1], st);
+    c->ev_used += 2;
+  }
+};
+
+template <typename T>
+da_status dalloc(da_ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return DA_OK;
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char buf[160];
+    snprintf(buf, sizeof buf, "cudaMalloc of %.3f GB failed: %s", count * sizeof(T) / 1e9, cudaGetErrorString(e));
+    return fail(c, DA_ENOMEM, buf);
+  }
+#ifdef DA_POISON_ALLOCATIONS
+  // debugging builds: every fresh allocation holds NaNs (0xff bytes), so a
+  // read of device memory that nothing wrote shows up as NaN in the results
+  cudaMemset(v, 0xff, count * sizeof(T));
+#endif
+  c->allocs.push_back(v);
+  c->bytes += count * sizeof(T);
+  *p = static_cast<T*>(v);
+  return DA_OK;
+}
+
+// Observation slot of step k, or -1 (host copy of the kernels' obs_slot).
+inline int obs_slot_host(const da_ctx* c, int k) {
+  if (k == 0) return c->obs.include_t0 ? 0 : -1;
+  if (k % c->obs.every) return -1;
+  return k / c->obs.every - 1 + (c->obs.include_t0 ? 1 : 0);
+}
+
+// Plan variant the autotuner chose for (n, batch) in this process, or 0
+// (plans.cu).
+int cached_plan(int n, int B);

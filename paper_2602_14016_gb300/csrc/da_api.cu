@@ -1,140 +1,16 @@
-// da_api.cu -- the C ABI of include/da.h: context, validation, buffers and
-// the launch sequence of the forward solve, the adjoint sweep and the
-// optimiser.  All arithmetic of the path runs in the kernels of
-// kernels.cuh / blas.cuh; this file only orders launches and moves scalars.
-#include <cuda_runtime.h>
-
-#include <cmath>
-#include <cstdio>
+// da_api.cu -- the C ABI of include/da.h: context creation and
+// validation, buffers, and the launch sequences of the forward solve, the
+// adjoint sweep and their variants (cost and gradient, vector-Jacobian
+// product, terminal adjoint, shell spectra).  The FFT plan variants and the
+// autotuner are in plans.cu, the optimiser in lbfgs.cu.  All arithmetic of
+// the path runs in the kernels of kernels.cuh; this file only orders
+// launches and moves scalars.
 #include <algorithm>
 #include <cstring>
-#include <map>
-#include <mutex>
-#include <string>
-#include <utility>
-#include <vector>
 
-#include "../../include/da.h"
-#include "blas.cuh"
-#include "linesearch.h"
-#include "ops.h"
+#include "ctx.h"
 
-using da::Dev;
-using da::Ops;
-
-struct da_ctx {
-  int device = 0;
-  int n = 0, nsteps = 0, ckpt = 0, B = 1;
-  double dt = 0, nu = 0;
-  da_forcing force{};
-  da_obs_operator obs{};
-  int nt = 0, P = 0;
-  const Ops* ops = nullptr;
-  Dev dev{};
-  std::vector<void*> allocs;
-  unsigned long long bytes = 0;
-  unsigned long long launches = 0;
-  bool have_obs = false;
-  bool have_adj = false;
-  bool have_fwd = false;  // a stored forward (stage fields / checkpoints) is valid
-  int nckpt = 0;          // checkpoints held (ckpt > 0)
-  double2* ckpt_buf = nullptr;
-  double sobolev = 0.0;   // lambda of the regularisation term of Eq. (4)
-  // shell lists of the adjoint spectra (built on the first da_adjoint_spectra)
-  int nshell = 0;
-  int *shell_off = nullptr, *shell_mode = nullptr;
-  double *shell_wgt = nullptr, *shell_scratch = nullptr;
-  double2* w0 = nullptr;  // compact initial state kept for that term
-  std::string err;
-  // optimiser buffers (allocated on first da_assimilate)
-  double *x = nullptr, *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr, *S = nullptr, *Y = nullptr;
-  double *part = nullptr, *dots = nullptr, *scal = nullptr;
-  void** ptrs = nullptr;
-  int mem = 0;
-  // CUDA-graph replay of da_cost_grad
-  bool use_graph = false;
-  cudaGraphExec_t cg_exec = nullptr;
-  unsigned long long cg_launches = 0;  // kernel nodes in the captured graph
-  cudaStream_t gstream = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  double *sbuf = nullptr, *gbuf = nullptr;
-  // event timing of one kernel class
-  int timed_class = 0;
-  std::vector<cudaEvent_t> ev;
-  size_t ev_used = 0;
-};
-
-static std::string g_create_error;
-
-#define DA_TRY_CUDA(ctx, call)                                                                    \
-  do {                                                                                            \
-    cudaError_t e_ = (call);                                                                      \
-    if (e_ != cudaSuccess) return fail((ctx), DA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
-
-static da_status fail(da_ctx* c, da_status s, const std::string& msg) {
-  if (c)
-    c->err = msg;
-  else
-    g_create_error = msg;
-  return s;
-}
-
-static da_status check_launch(da_ctx* c, unsigned long long nlaunch = 1) {
-  c->launches += nlaunch;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(c, DA_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
-  return DA_OK;
-}
-
-// Brackets one launch of kernel class `cls` with events when that class is timed.
-struct Timed {
-  da_ctx* c;
-  bool on;
-  cudaStream_t st;
-  Timed(da_ctx* c_, int cls, cudaStream_t s) : c(c_), on(c_->timed_class == cls), st(s) {
-    if (!on) return;
-    if (c->ev_used + 2 > c->ev.size()) {
-      for (int i = 0; i < 256; ++i) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) {
-          on = false;
-          return;
-        }
-        c->ev.push_back(e);
-      }
-    }
-    cudaEventRecord(c->ev[c->ev_used], st);
-  }
-  ~Timed() {
-    if (!on) return;
-    cudaEventRecord(c->ev[c->ev_used + 1], st);
-    c->ev_used += 2;
-  }
-};
-
-template <typename T>
-static da_status dalloc(da_ctx* c, T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) return DA_OK;
-  void* v = nullptr;
-  cudaError_t e = cudaMalloc(&v, count * sizeof(T));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    char buf[160];
-    snprintf(buf, sizeof buf, "cudaMalloc of %.3f GB failed: %s", count * sizeof(T) / 1e9, cudaGetErrorString(e));
-    return fail(c, DA_ENOMEM, buf);
-  }
-#ifdef DA_POISON_ALLOCATIONS
-  // debugging builds: every fresh allocation holds NaNs (0xff bytes), so a
-  // read of device memory that nothing wrote shows up as NaN in the results
-  cudaMemset(v, 0xff, count * sizeof(T));
-#endif
-  c->allocs.push_back(v);
-  c->bytes += count * sizeof(T);
-  *p = static_cast<T*>(v);
-  return DA_OK;
-}
+std::string g_create_error;
 
 // exp(-2 pi i t / m), t < m, rounded from long double.
 static std::vector<double2> roots_of_unity(int m) {
@@ -145,23 +21,6 @@ static std::vector<double2> roots_of_unity(int m) {
     w[t] = make_double2((double)cosl(a), (double)sinl(a));
   }
   return w;
-}
-
-// Plan variant chosen by the autotuner per (grid size, batch), for the
-// contexts created afterwards in this process.
-static std::mutex g_plan_mu;
-static std::map<std::pair<int, int>, int> g_plan_choice;
-
-static int cached_plan(int n, int B) {
-  std::lock_guard<std::mutex> lock(g_plan_mu);
-  auto it = g_plan_choice.find({n, B});
-  return it == g_plan_choice.end() ? 0 : it->second;
-}
-
-static int obs_slot_host(const da_ctx* c, int k) {
-  if (k == 0) return c->obs.include_t0 ? 0 : -1;
-  if (k % c->obs.every) return -1;
-  return k / c->obs.every - 1 + (c->obs.include_t0 ? 1 : 0);
 }
 
 extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, const da_forcing* forcing,
@@ -601,124 +460,6 @@ extern "C" da_status da_set_graphs(da_ctx* c, int enable) {
   return DA_OK;
 }
 
-// Switches the context's pass kernels to plan variant v: launchers, folded
-// twiddle table, shared-memory attributes.  A captured graph holds the old
-// kernels and is dropped; a stored forward trajectory is invalidated.
-static da_status set_plan(da_ctx* c, int v) {
-  const Ops* o = da::ops_for(c->n, v);
-  if (!o) return fail(c, DA_EINVAL, "plan variant out of range (da_plan_count)");
-  if (o == c->ops) return DA_OK;
-  std::vector<double> fold(o->fold_doubles);
-  o->fold_table(fold.data());
-  DA_TRY_CUDA(c, cudaMemcpy((void*)c->dev.fold, fold.data(), fold.size() * sizeof(double), cudaMemcpyHostToDevice));
-  DA_TRY_CUDA(c, o->setup());
-  c->ops = o;
-  if (c->cg_exec) {
-    cudaGraphExecDestroy(c->cg_exec);
-    c->cg_exec = nullptr;
-  }
-  c->have_fwd = false;
-  return DA_OK;
-}
-
-extern "C" int da_plan_count(int n) { return da::ops_for(n) ? da::plan_count(n) : 0; }
-
-extern "C" int da_get_plan(const da_ctx* c) { return c ? c->ops->variant : -1; }
-
-extern "C" da_status da_set_plan(da_ctx* c, int variant) {
-  if (!c) return fail(c, DA_EINVAL, "ctx must not be NULL");
-  // the folded table and the launchers change under any work in flight
-  DA_TRY_CUDA(c, cudaDeviceSynchronize());
-  return set_plan(c, variant);
-}
-
-// Zeroes the working state that the tuning passes run over.
-static da_status clear_state(da_ctx* c, cudaStream_t st) {
-  const Dev& d = c->dev;
-  const size_t comp = (size_t)c->B * c->ops->Kr * c->ops->Kc * sizeof(double2);
-  const size_t mixed = (size_t)c->B * 2 * c->n * c->ops->Kc * sizeof(double2);
-  for (void* p : {(void*)d.W, (void*)d.Acc, (void*)d.Y, (void*)d.KB, (void*)d.LamBar, (void*)d.Sum})
-    DA_TRY_CUDA(c, cudaMemsetAsync(p, 0, comp, st));
-  DA_TRY_CUDA(c, cudaMemsetAsync(d.Mx, 0, mixed, st));
-  DA_TRY_CUDA(c, cudaMemsetAsync(d.Mn, 0, mixed, st));
-  return DA_OK;
-}
-
-// `steps` RK steps of the pass kernels (forward, and the adjoint when the
-// context stores stage fields) over whatever the working buffers hold.
-static da_status tuning_steps(da_ctx* c, int steps, cudaStream_t st) {
-  const Ops* o = c->ops;
-  Dev& d = c->dev;
-  const bool store = d.traj != nullptr;
-  d.seg0 = 0;
-  for (int i = 0; i < steps; ++i) {
-    const int k = store ? i % d.traj_steps : 0;
-    for (int j = 1; j <= 4; ++j) {
-      o->fwd_rows(d, k, j, store ? da::F_STORE : 0, st);
-      o->fwd_cols(d, j, 0, st);
-    }
-    if (store)
-      for (int j = 4; j >= 1; --j) {
-        o->adj_rows(d, k, j, st);
-        o->adj_cols(d, k, j, 0, st);
-      }
-    da_status r = check_launch(c, store ? 16 : 8);
-    if (r) return r;
-  }
-  return DA_OK;
-}
-
-extern "C" da_status da_autotune(da_ctx* c, int steps, int* chosen, double* ms_per_step) {
-  if (!c) return fail(c, DA_EINVAL, "ctx must not be NULL");
-  if (steps < 1) return fail(c, DA_EINVAL, "steps must be >= 1");
-  // the tuning passes overwrite the working state: let every evaluation in
-  // flight on any stream finish first
-  DA_TRY_CUDA(c, cudaDeviceSynchronize());
-  cudaStream_t st = nullptr;
-  DA_TRY_CUDA(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  da_status r = DA_OK;
-  int best = 0;
-  float best_ms = 0.f;
-  auto cuda = [&](cudaError_t e, const char* what) {
-    if (r == DA_OK && e != cudaSuccess) r = fail(c, DA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
-  };
-  cuda(cudaEventCreate(&e0), "event");
-  cuda(cudaEventCreate(&e1), "event");
-  for (int v = 0; r == DA_OK && v < da::plan_count(c->n); ++v) {
-    if ((r = set_plan(c, v))) break;
-    if ((r = clear_state(c, st))) break;
-    if ((r = tuning_steps(c, 1, st))) break;  // warm-up
-    cuda(cudaEventRecord(e0, st), "event record");
-    if (r || (r = tuning_steps(c, steps, st))) break;
-    cuda(cudaEventRecord(e1, st), "event record");
-    cuda(cudaEventSynchronize(e1), "event synchronize");
-    float ms = 0.f;
-    cuda(cudaEventElapsedTime(&ms, e0, e1), "event elapsed time");
-    if (r) break;
-    ms /= steps;
-    if (ms_per_step) ms_per_step[v] = ms;
-    if (v == 0 || ms < best_ms) {
-      best = v;
-      best_ms = ms;
-    }
-  }
-  if (r == DA_OK) r = set_plan(c, best);
-  if (r == DA_OK) r = clear_state(c, st);
-  if (r == DA_OK) cuda(cudaStreamSynchronize(st), "stream synchronize");
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
-  cudaStreamDestroy(st);
-  if (r) return r;
-  {
-    std::lock_guard<std::mutex> lock(g_plan_mu);
-    g_plan_choice[{c->n, c->B}] = best;
-  }
-  c->have_fwd = false;
-  if (chosen) *chosen = best;
-  return DA_OK;
-}
-
 extern "C" da_status da_cost_grad(da_ctx* c, const double* s, double* J, double* grad_s, void* stream) {
   if (!c || !s) return fail(c, DA_EINVAL, "ctx and s must not be NULL");
   if (!c->have_obs) return fail(c, DA_EINVAL, "no observations: call da_set_observations first");
@@ -896,333 +637,4 @@ extern "C" da_status da_control_from_omega(da_ctx* c, const double* omega0, doub
   c->ops->spec_to_mixed(c->dev, c->dev.Y, da::M_INV_CTRL, st);
   c->ops->c2r_rows(c->dev, s, st);
   return check_launch(c, 3);
-}
-
-// ---------------------------------------------------------------------------
-// L-BFGS driver (Sec. II.C: L-BFGS on the transformed control in the
-// Euclidean metric).  Members advance in lockstep: every cost-gradient
-// evaluation serves all members, and a member that is not searching
-// re-evaluates its accepted point, which changes nothing.  Each member keeps
-// a ring of memory+1 vector slots for its (s, y) pairs, so a new pair can be
-// formed and tested before the oldest one is dropped.
-// ---------------------------------------------------------------------------
-
-namespace {
-
-struct Vec {
-  da_ctx* c;
-  cudaStream_t st;
-  size_t len;
-
-  // out[b] = a_b . x_b (NULL pointer: 0)
-  da_status dot(const std::vector<const double*>& a, const std::vector<const double*>& x, std::vector<double>& out) {
-    const int B = c->B;
-    std::vector<const double*> ptrs(2 * B);
-    for (int b = 0; b < B; ++b) {
-      ptrs[b] = a[b];
-      ptrs[B + b] = x[b];
-    }
-    DA_TRY_CUDA(c, cudaMemcpyAsync(c->ptrs, ptrs.data(), 2 * B * sizeof(void*), cudaMemcpyHostToDevice, st));
-    const int chunks = da::dot_chunks(len);
-    da::k_dot_partial<<<dim3(chunks, B), 256, 0, st>>>((const double* const*)c->ptrs,
-                                                        (const double* const*)c->ptrs + B, c->part, len);
-    da::k_dot_final<<<B, 256, 0, st>>>(c->part, c->dots, chunks);
-    da_status r = check_launch(c, 2);
-    if (r) return r;
-    out.assign(B, 0.0);
-    DA_TRY_CUDA(c, cudaMemcpyAsync(out.data(), c->dots, B * sizeof(double), cudaMemcpyDeviceToHost, st));
-    DA_TRY_CUDA(c, cudaStreamSynchronize(st));
-    return DA_OK;
-  }
-
-  // y_b = alpha_b x_b + beta_b y_b (NULL pointer: member untouched)
-  da_status axpby(const std::vector<double>& alpha, const std::vector<const double*>& x,
-                  const std::vector<double>& beta, const std::vector<double*>& y) {
-    const int B = c->B;
-    std::vector<const void*> ptrs(2 * B);
-    std::vector<double> ab(2 * B);
-    for (int b = 0; b < B; ++b) {
-      ptrs[b] = x[b];
-      ptrs[B + b] = y[b];
-      ab[b] = alpha[b];
-      ab[B + b] = beta[b];
-    }
-    DA_TRY_CUDA(c, cudaMemcpyAsync(c->ptrs, ptrs.data(), 2 * B * sizeof(void*), cudaMemcpyHostToDevice, st));
-    DA_TRY_CUDA(c, cudaMemcpyAsync(c->scal, ab.data(), 2 * B * sizeof(double), cudaMemcpyHostToDevice, st));
-    da::k_axpby<<<dim3((unsigned)((len + 1023) / 1024), B), 256, 0, st>>>(
-        (const double* const*)c->ptrs, (double* const*)c->ptrs + B, c->scal, c->scal + B, len);
-    da_status r = check_launch(c);
-    if (r) return r;
-    DA_TRY_CUDA(c, cudaStreamSynchronize(st));  // host arrays must outlive the copies
-    return DA_OK;
-  }
-
-  double* member(double* base, int b) const { return base + (size_t)b * len; }
-};
-
-struct Member {
-  std::vector<int> pairs;    // slot indices, oldest first (at most `memory`)
-  std::vector<double> rho;   // 1 / (s . y) per pair
-  double f = 0, gnorm = 0, g0norm = 0;
-  int state = 0;             // 0 active, 1 converged, 2 line-search failure, 3 diverged
-  int iters = 0;
-};
-
-}  // namespace
-
-extern "C" da_status da_assimilate(da_ctx* c, double* s, int max_iter, const da_lbfgs_opts* opts, double* J_hist,
-                                   int* iters_done, void* stream) {
-  if (!c || !s || !J_hist || !iters_done || max_iter < 0) return fail(c, DA_EINVAL, "bad arguments");
-  if (!c->have_obs) return fail(c, DA_EINVAL, "no observations: call da_set_observations first");
-  if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
-  cudaStream_t st = (cudaStream_t)stream;
-  da_lbfgs_opts o{10, 1e-4, 0.9, 1e-10, 20};
-  if (opts) {
-    if (opts->memory > 0) o.memory = opts->memory;
-    if (opts->c1 > 0) o.c1 = opts->c1;
-    if (opts->c2 > 0) o.c2 = opts->c2;
-    if (opts->gtol_rel > 0) o.gtol_rel = opts->gtol_rel;
-    if (opts->max_ls_evals > 0) o.max_ls_evals = opts->max_ls_evals;
-  }
-  const int B = c->B, m = o.memory, slots = m + 1;
-  const size_t len = (size_t)c->n * c->n;
-  da_status r = DA_OK;
-  if (c->mem != m) {
-    if (c->mem) return fail(c, DA_EINVAL, "memory must stay the same across calls on one context");
-    auto A = [&](da_status x) {
-      if (r == DA_OK) r = x;
-    };
-    A(dalloc(c, &c->x, B * len));
-    A(dalloc(c, &c->g, B * len));
-    A(dalloc(c, &c->d, B * len));
-    A(dalloc(c, &c->xt, B * len));
-    A(dalloc(c, &c->gt, B * len));
-    A(dalloc(c, &c->S, (size_t)slots * B * len));
-    A(dalloc(c, &c->Y, (size_t)slots * B * len));
-    A(dalloc(c, &c->part, (size_t)B * da::dot_chunks(len)));
-    A(dalloc(c, &c->dots, (size_t)B));
-    A(dalloc(c, &c->scal, (size_t)2 * B));
-    A(dalloc<void*>(c, &c->ptrs, (size_t)2 * B));
-    if (r) return r;
-    c->mem = m;
-  }
-  Vec V{c, st, len};
-  auto Sslot = [&](int slot, int b) { return c->S + ((size_t)slot * B + b) * len; };
-  auto Yslot = [&](int slot, int b) { return c->Y + ((size_t)slot * B + b) * len; };
-  const std::vector<double> zeros(B, 0.0), ones(B, 1.0);
-  std::vector<Member> mb(B);
-  std::vector<double> f(B), tmp;
-  std::vector<const double*> pa(B), pb(B);
-  std::vector<double*> py(B);
-
-  DA_TRY_CUDA(c, cudaMemcpyAsync(c->x, s, B * len * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  if ((r = da_cost_grad(c, c->x, f.data(), c->g, st))) return r;
-  for (int b = 0; b < B; ++b) pa[b] = V.member(c->g, b);
-  if ((r = V.dot(pa, pa, tmp))) return r;
-  for (int b = 0; b < B; ++b) {
-    mb[b].f = f[b];
-    mb[b].g0norm = mb[b].gnorm = std::sqrt(tmp[b]);
-    if (!std::isfinite(f[b]) || !std::isfinite(tmp[b])) mb[b].state = 3;
-    J_hist[(size_t)b * (max_iter + 1)] = f[b];
-  }
-
-  for (int it = 0; it < max_iter; ++it) {
-    bool any = false;
-    for (int b = 0; b < B; ++b) {
-      if (mb[b].state == 0 && mb[b].gnorm <= o.gtol_rel * mb[b].g0norm) mb[b].state = 1;
-      any |= mb[b].state == 0;
-    }
-    if (!any) break;
-    auto active = [&](int b) { return mb[b].state == 0; };
-
-    // d = -H g by the two-loop recursion (d carries -q)
-    for (int b = 0; b < B; ++b) {
-      pa[b] = active(b) ? V.member(c->g, b) : nullptr;
-      py[b] = active(b) ? V.member(c->d, b) : nullptr;
-    }
-    std::vector<double> minus(B, -1.0);
-    if ((r = V.axpby(minus, pa, zeros, py))) return r;
-    int hmax = 0;
-    for (int b = 0; b < B; ++b)
-      if (active(b)) hmax = std::max(hmax, (int)mb[b].pairs.size());
-    std::vector<std::vector<double>> alpha(B, std::vector<double>(hmax, 0.0));
-    for (int h = 0; h < hmax; ++h) {  // newest to oldest
-      for (int b = 0; b < B; ++b) {
-        const int cnt = (int)mb[b].pairs.size();
-        const bool use = active(b) && h < cnt;
-        pa[b] = use ? Sslot(mb[b].pairs[cnt - 1 - h], b) : nullptr;
-        pb[b] = use ? V.member(c->d, b) : nullptr;
-      }
-      if ((r = V.dot(pa, pb, tmp))) return r;
-      std::vector<double> al(B, 0.0);
-      for (int b = 0; b < B; ++b) {
-        const int cnt = (int)mb[b].pairs.size();
-        const bool use = active(b) && h < cnt;
-        if (use) al[b] = alpha[b][h] = -mb[b].rho[cnt - 1 - h] * tmp[b];  // rho s.q
-        pa[b] = use ? Yslot(mb[b].pairs[cnt - 1 - h], b) : nullptr;
-        py[b] = use ? V.member(c->d, b) : nullptr;
-      }
-      if ((r = V.axpby(al, pa, ones, py))) return r;  // q -= alpha y
-    }
-    if (hmax > 0) {  // H0 = (s.y / y.y) I from the newest pair
-      for (int b = 0; b < B; ++b) {
-        const bool use = active(b) && !mb[b].pairs.empty();
-        pa[b] = use ? Yslot(mb[b].pairs.back(), b) : nullptr;
-      }
-      if ((r = V.dot(pa, pa, tmp))) return r;
-      std::vector<double> gam(B, 1.0);
-      for (int b = 0; b < B; ++b) {
-        const bool use = active(b) && !mb[b].pairs.empty();
-        if (use) gam[b] = 1.0 / (mb[b].rho.back() * tmp[b]);
-        pa[b] = use ? V.member(c->d, b) : nullptr;
-        py[b] = use ? V.member(c->d, b) : nullptr;
-      }
-      if ((r = V.axpby(zeros, pa, gam, py))) return r;
-    }
-    for (int h = hmax - 1; h >= 0; --h) {  // oldest to newest
-      for (int b = 0; b < B; ++b) {
-        const int cnt = (int)mb[b].pairs.size();
-        const bool use = active(b) && h < cnt;
-        pa[b] = use ? Yslot(mb[b].pairs[cnt - 1 - h], b) : nullptr;
-        pb[b] = use ? V.member(c->d, b) : nullptr;
-      }
-      if ((r = V.dot(pa, pb, tmp))) return r;
-      std::vector<double> al(B, 0.0);
-      for (int b = 0; b < B; ++b) {
-        const int cnt = (int)mb[b].pairs.size();
-        const bool use = active(b) && h < cnt;
-        if (use) al[b] = -(alpha[b][h] - (-mb[b].rho[cnt - 1 - h] * tmp[b]));  // r += (alpha - beta) s
-        pa[b] = use ? Sslot(mb[b].pairs[cnt - 1 - h], b) : nullptr;
-        py[b] = use ? V.member(c->d, b) : nullptr;
-      }
-      if ((r = V.axpby(al, pa, ones, py))) return r;
-    }
-    for (int b = 0; b < B; ++b) {
-      pa[b] = active(b) ? V.member(c->g, b) : nullptr;
-      pb[b] = active(b) ? V.member(c->d, b) : nullptr;
-    }
-    std::vector<double> gd;
-    if ((r = V.dot(pa, pb, gd))) return r;
-    {
-      std::vector<double> al(B, 0.0);
-      bool reset = false;
-      for (int b = 0; b < B; ++b) {
-        pa[b] = nullptr;
-        py[b] = nullptr;
-        if (active(b) && !(gd[b] < 0.0)) {  // not a descent direction: restart from -g
-          mb[b].pairs.clear();
-          mb[b].rho.clear();
-          al[b] = -1.0;
-          pa[b] = V.member(c->g, b);
-          py[b] = V.member(c->d, b);
-          gd[b] = -mb[b].gnorm * mb[b].gnorm;
-          reset = true;
-        }
-      }
-      if (reset && (r = V.axpby(al, pa, zeros, py))) return r;
-    }
-
-    // line search, all searching members together
-    std::vector<da::MoreThuente> ls(B);
-    std::vector<int> searching(B, 0);
-    for (int b = 0; b < B; ++b) {
-      if (!active(b)) continue;
-      const double s0 = it == 0 ? std::min(1.0, 1.0 / mb[b].gnorm) : 1.0;
-      ls[b].start(mb[b].f, gd[b], s0, o.c1, o.c2, 1e-10, 1e-20, 1e20, o.max_ls_evals);
-      searching[b] = 1;
-    }
-    std::vector<double> ft(B), dg;
-    for (;;) {
-      bool anys = false;
-      for (int b = 0; b < B; ++b) anys |= searching[b] != 0;
-      if (!anys) break;
-      // xt = x + stp d for searching members, x otherwise
-      DA_TRY_CUDA(c, cudaMemcpyAsync(c->xt, c->x, B * len * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      std::vector<double> al(B, 0.0);
-      for (int b = 0; b < B; ++b) {
-        al[b] = searching[b] ? ls[b].stp() : 0.0;
-        pa[b] = searching[b] ? V.member(c->d, b) : nullptr;
-        py[b] = searching[b] ? V.member(c->xt, b) : nullptr;
-      }
-      if ((r = V.axpby(al, pa, ones, py))) return r;
-      if ((r = da_cost_grad(c, c->xt, ft.data(), c->gt, st))) return r;
-      for (int b = 0; b < B; ++b) {
-        pa[b] = searching[b] ? V.member(c->gt, b) : nullptr;
-        pb[b] = searching[b] ? V.member(c->d, b) : nullptr;
-      }
-      if ((r = V.dot(pa, pb, dg))) return r;
-      for (int b = 0; b < B; ++b) {
-        if (!searching[b]) continue;
-        if (!std::isfinite(ft[b]) || !std::isfinite(dg[b])) {
-          searching[b] = 0;
-          mb[b].state = 3;
-          continue;
-        }
-        const int act = ls[b].step(ft[b], dg[b]);
-        if (act == da::MoreThuente::EVALUATE) continue;
-        searching[b] = 0;
-        const bool ok = act == da::MoreThuente::CONVERGED;
-        if (ok || ft[b] < mb[b].f) {
-          // accept: new pair in a free slot, s = xt - x, y = gt - g
-          int freeslot = 0;
-          for (int t = 0; t < slots; ++t)
-            if (std::find(mb[b].pairs.begin(), mb[b].pairs.end(), t) == mb[b].pairs.end()) {
-              freeslot = t;
-              break;
-            }
-          double* Sd = Sslot(freeslot, b);
-          double* Yd = Yslot(freeslot, b);
-          DA_TRY_CUDA(c, cudaMemcpyAsync(Sd, V.member(c->xt, b), len * sizeof(double), cudaMemcpyDeviceToDevice, st));
-          DA_TRY_CUDA(c, cudaMemcpyAsync(Yd, V.member(c->gt, b), len * sizeof(double), cudaMemcpyDeviceToDevice, st));
-          std::vector<double> neg(B, 0.0);
-          std::vector<const double*> xs(B, nullptr);
-          std::vector<double*> ys(B, nullptr);
-          neg[b] = -1.0;
-          xs[b] = V.member(c->x, b);
-          ys[b] = Sd;
-          if ((r = V.axpby(neg, xs, ones, ys))) return r;
-          xs[b] = V.member(c->g, b);
-          ys[b] = Yd;
-          if ((r = V.axpby(neg, xs, ones, ys))) return r;
-          std::vector<const double*> sa(B, nullptr), ya(B, nullptr);
-          sa[b] = Sd;
-          ya[b] = Yd;
-          std::vector<double> sy, yy;
-          if ((r = V.dot(sa, ya, sy))) return r;
-          if ((r = V.dot(ya, ya, yy))) return r;
-          if (sy[b] > 1e-16 * yy[b]) {
-            if ((int)mb[b].pairs.size() == m) {
-              mb[b].pairs.erase(mb[b].pairs.begin());
-              mb[b].rho.erase(mb[b].rho.begin());
-            }
-            mb[b].pairs.push_back(freeslot);
-            mb[b].rho.push_back(1.0 / sy[b]);
-          }
-          DA_TRY_CUDA(c, cudaMemcpyAsync(V.member(c->x, b), V.member(c->xt, b), len * sizeof(double),
-                                         cudaMemcpyDeviceToDevice, st));
-          DA_TRY_CUDA(c, cudaMemcpyAsync(V.member(c->g, b), V.member(c->gt, b), len * sizeof(double),
-                                         cudaMemcpyDeviceToDevice, st));
-          mb[b].f = ft[b];
-          mb[b].iters = it + 1;
-          J_hist[(size_t)b * (max_iter + 1) + it + 1] = ft[b];
-        }
-        if (!ok) mb[b].state = 2;
-      }
-    }
-    for (int b = 0; b < B; ++b) pa[b] = V.member(c->g, b);
-    if ((r = V.dot(pa, pa, tmp))) return r;
-    for (int b = 0; b < B; ++b) mb[b].gnorm = std::sqrt(tmp[b]);
-  }
-  bool diverged = false, failed = false;
-  for (int b = 0; b < B; ++b) {
-    iters_done[b] = mb[b].iters;
-    for (int it = mb[b].iters + 1; it <= max_iter; ++it) J_hist[(size_t)b * (max_iter + 1) + it] = mb[b].f;
-    diverged |= mb[b].state == 3;
-    failed |= mb[b].state == 2;
-  }
-  DA_TRY_CUDA(c, cudaMemcpyAsync(s, c->x, B * len * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  DA_TRY_CUDA(c, cudaStreamSynchronize(st));
-  if (diverged) return fail(c, DA_EDIVERGED, "non-finite cost or gradient");
-  if (failed) return fail(c, DA_ENOTCONV, "line search failed (step-size collapse)");
-  return DA_OK;
 }
