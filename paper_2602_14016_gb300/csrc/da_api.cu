@@ -556,7 +556,7 @@ static da_status build_shells(da_ctx* c) {
       const double k2 = (double)kx * kx + (double)ky * ky;
       if (k2 == 0.0) continue;
       const int sh = (int)std::floor(std::sqrt(k2));
-      modes[sh].push_back(r * Kc + kx);
+      modes[sh].push_back(kx * Kr + r);  // compact arrays are column-major
       wgts[sh].push_back((kx == 0 ? 1.0 : 2.0) * k2 / (2.0 * n4));
     }
   std::vector<int> off(nshell + 1, 0), mode;

@@ -1,9 +1,11 @@
 // kernels.cuh -- pass kernels of the cost-and-gradient evaluation.
 //
 // Layout (per member b of a batch):
-//   compact spectra  [Kr][Kc] complex: the retained set of the 2/3 rule,
-//                    kx = 0..K (columns), compact row r -> ky = r (r <= K)
-//                    or r - Kr; K = floor((N-1)/3), Kc = K+1, Kr = 2K+1.
+//   compact spectra  [Kc][Kr] complex, column-major (cidx): the retained
+//                    set of the 2/3 rule, kx = 0..K (columns), compact row
+//                    r -> ky = r (r <= K) or r - Kr; K = floor((N-1)/3),
+//                    Kc = K+1, Kr = 2K+1.  A column pass reads and writes one
+//                    contiguous column.
 //   mixed fields     [2][N][Kc] complex: physical y, spectral kx (the
 //                    transform along y of a compact column), two fields.
 //   stage fields     [nsteps][4 stages][2 fields][N][N] double: u, v of
@@ -74,7 +76,7 @@ struct Dev {
   int force;
   double amp;
   int nf;
-  double2 *W, *Acc, *Y, *KB, *LamBar, *Sum;  // compact [B][Kr][Kc]
+  double2 *W, *Acc, *Y, *KB, *LamBar, *Sum;  // compact [B][Kc][Kr] (cidx)
   double2* Mx;                               // mixed [B][2][N][Kc]: column-pass output
   double2* Mn;                               // mixed [B][2][N][Kc]: row-pass output
   double* traj;                              // [B][traj_steps][4][2][N][N]
@@ -84,7 +86,7 @@ struct Dev {
   const double* mobs;                        // data [B][nt][P2][2]
   double* res;                               // residuals [B][nt][P2][2]
   double* J;                                 // [B]
-  const double* mult;                        // control multiplier |k| W^1/2, [B][Kr][Kc]
+  const double* mult;                        // control multiplier |k| W^1/2, compact [B][Kc][Kr]
   const double* fold;                        // folded twiddles of Plan<N> (fft.cuh)
   const double2* twP;                        // W_P^t, t < P
   const Sym4* symF;                          // [Kc][Kr] su, sv, cp, cq
@@ -111,6 +113,12 @@ struct Geo {
 };
 
 __device__ __forceinline__ int ky_of_row(int r, int K) { return r <= K ? r : r - (2 * K + 1); }
+
+// Index of mode (row r, column kx) of member bm in a compact array.
+template <int N>
+__host__ __device__ __forceinline__ size_t cidx(int bm, int r, int kx) {
+  return ((size_t)bm * Geo<N>::Kc + kx) * Geo<N>::Kr + r;
+}
 
 template <int N, int V = 0>
 __device__ __forceinline__ void load_fold(double* T, const double* __restrict__ g) {
@@ -256,7 +264,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_spec_to_mixed(Dev d, con
     double2 v = make_double2(0.0, 0.0);
     if (ky >= -G::K && ky <= G::K) {
       const int r = ky >= 0 ? ky : ky + G::Kr;
-      const size_t idx = ((size_t)bm * G::Kr + r) * G::Kc + kx;
+      const size_t idx = cidx<N>(bm, r, kx);
       const double m = d.mult[idx];
       double f;
       if (mode == M_ONE) f = 1.0;
@@ -285,7 +293,7 @@ __global__ void k_compact_to_half(const double2* __restrict__ src, double2* __re
     double2 v = make_double2(0.0, 0.0);
     if (p <= G::K && ky >= -G::K && ky <= G::K) {
       const int r = ky >= 0 ? ky : ky + G::Kr;
-      v = src[((size_t)bm * G::Kr + r) * G::Kc + p];
+      v = src[cidx<N>(bm, r, p)];
     }
     out[(size_t)bm * N * G::NH + i] = v;
   }
@@ -296,7 +304,7 @@ __global__ void k_half_to_compact(const double2* __restrict__ in, double2* __res
   using G = Geo<N, V>;
   const int bm = blockIdx.y;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G::Kr * G::Kc; i += gridDim.x * blockDim.x) {
-    const int r = i / G::Kc, kx = i - r * G::Kc;
+    const int kx = i / G::Kr, r = i - kx * G::Kr;
     const int ky = ky_of_row(r, G::K);
     dst[(size_t)bm * G::Kr * G::Kc + i] = in[((size_t)bm * N + (ky & (N - 1))) * G::NH + kx];
   }
@@ -406,7 +414,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_ctrl_cols(Dev d, int fla
   #pragma unroll
   for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
     const int ky = ky_of_row(rr, G::K);
-    const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+    const size_t idx = cidx<N>(bm, rr, kx);
     const double2 w0 = cscale(a[ky & (N - 1)], d.mult[idx]);
     d.W[idx] = w0;
     d.Y[idx] = w0;
@@ -433,7 +441,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_state_cols(Dev d) {
   #pragma unroll
   for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
     const int ky = ky_of_row(rr, G::K);
-    const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+    const size_t idx = cidx<N>(bm, rr, kx);
     const double2 w = d.W[idx];
     d.Y[idx] = w;
     put_stage_columns<N>(a, ky & (N - 1), d.symF[kx * G::Kr + rr], w);
@@ -522,7 +530,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_cols(Dev d, int stag
   auto load_inputs = [&](int t) {
     const int rr = threadIdx.x + t * G::THREADS;
     if (rr < G::Kr) {
-      const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+      const size_t idx = cidx<N>(bm, rr, kx);
       yv[t] = d.Y[idx];
       wv[t] = d.W[idx];
       accv[t] = stage > 1 ? d.Acc[idx] : make_double2(0.0, 0.0);
@@ -547,7 +555,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_cols(Dev d, int stag
     if constexpr (!G::PREFETCH) load_inputs(t);
     const int ky = ky_of_row(rr, G::K);
     const int qi = ky & (N - 1);
-    const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+    const size_t idx = cidx<N>(bm, rr, kx);
     const double2 ph = a[qi], qh = a[N + qi];
     // F = -(cp P + cq Q) - nu k^2 y
     double2 F = make_double2(-fma(f[t].c, ph.x, fma(f[t].d, qh.x, nk2[t] * yv[t].x)),
@@ -667,7 +675,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_init(Dev d, int mode
   #pragma unroll
   for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
     const int ky = ky_of_row(rr, G::K);
-    const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+    const size_t idx = cidx<N>(bm, rr, kx);
     double2 kb;
     if (resume) {
       kb = d.KB[idx];
@@ -745,7 +753,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_cols(Dev d, int n, i
   auto load_inputs = [&](int t) {
     const int rr = threadIdx.x + t * G::THREADS;
     if (rr < G::Kr) {
-      const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+      const size_t idx = cidx<N>(bm, rr, kx);
       kbv[t] = d.KB[idx];
       lbv[t] = d.LamBar[idx];
       sumv[t] = stage < 4 ? d.Sum[idx] : make_double2(0.0, 0.0);
@@ -771,7 +779,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_cols(Dev d, int n, i
     if constexpr (!G::PREFETCH) load_inputs(t);
     const int ky = ky_of_row(rr, G::K);
     const int qi = ky & (N - 1);
-    const size_t idx = ((size_t)bm * G::Kr + rr) * G::Kc + kx;
+    const size_t idx = cidx<N>(bm, rr, kx);
     const double2 Ru = a[qi], Rv = a[N + qi];
     // t = (-i ky/k^2) Ru + (i kx/k^2) Rv (the 1/2 of the row unpack in a1, c1)
     const double2 tt = make_double2(fma(g[t].a, Ru.y, -g[t].b * Rv.y), fma(-g[t].a, Ru.x, g[t].b * Rv.x));
@@ -814,7 +822,7 @@ __global__ void k_make_mult(double* __restrict__ mult, const int* __restrict__ k
   using G = Geo<N, V>;
   const int bm = blockIdx.y;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G::Kr * G::Kc; i += gridDim.x * blockDim.x) {
-    const int r = i / G::Kc, kx = i - r * G::Kc;
+    const int kx = i / G::Kr, r = i - kx * G::Kr;
     const int ky = ky_of_row(r, G::K);
     const double k2 = (double)(kx * kx + ky * ky);
     const double k = sqrt(k2);

@@ -32,7 +32,7 @@ __global__ void k_sobolev_cost(double* J, const double2* w0, double lambda, int 
   const double2* w = w0 + (size_t)bm * Kr * Kc;
   double acc = 0.0;
   for (int i = threadIdx.x; i < Kr * Kc; i += blockDim.x) {
-    const double wt = (i % Kc) == 0 ? 1.0 : 2.0;  // kx > 0 stands for +-kx
+    const double wt = i < Kr ? 1.0 : 2.0;  // column-major: i < Kr is kx = 0; kx > 0 stands for +-kx
     acc = fma(wt, w[i].x * w[i].x + w[i].y * w[i].y, acc);
   }
   __shared__ double red[256];
