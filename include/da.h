@@ -195,7 +195,7 @@ da_status da_set_plan(da_ctx* ctx, int variant);
  * process.  chosen (nullable): HOST int, the variant taken; ms_per_step
  * (nullable): HOST double[da_plan_count(n)], the measured milliseconds per
  * step of each variant.  Synchronous (it first waits for all work on the
- * device, then runs on a stream of its own); it overwrites the context's state and
+ * device, then runs on the legacy default stream); it overwrites the context's state and
  * stored trajectory, so call it before the evaluations (observations set by
  * da_set_observations are kept).  DA_EINVAL for steps < 1. */
 da_status da_autotune(da_ctx* ctx, int steps, int* chosen, double* ms_per_step);
