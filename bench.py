@@ -53,8 +53,8 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # (256^2, batch 7), from one ncu capture of the same launch configuration on
 # a 40-step window (per-launch data are the same for any window length);
 # valid only for the kernel sources they were taken from.
-TRAFFIC = {"src_hash": "d6986af3ef0e5680", "adj_rows": 12299264, "adj_cols": 10526464, "fwd_rows": 4971520,
-           "fwd_cols": 10492160}
+TRAFFIC = {"src_hash": "14357bce6796f53e", "adj_rows": 12299264, "adj_cols": 10526976, "fwd_rows": 4971264,
+           "fwd_cols": 10492928}
 
 
 def src_hash() -> str:
