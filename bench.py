@@ -471,6 +471,11 @@ def run_workload(args):
         out = workloads.autograd_check(api, torch, n=args.ag_n, nsteps=args.ag_steps, ckpt_every=64,
                                        directions=args.ag_dirs)
         line.update({"metric": "autograd gradient vs central differences", **out})
+    elif args.workload == "grids":
+        rows = workloads.grid_sweep(api, torch)
+        line.update({"metric": "fwd+adjoint gridpoint-steps/s FP64 per grid size and batch", "unit": UNIT,
+                     "rows": rows, "config": {"flow": "decaying, nu 1e-3", "probes": "8x8 every 10 steps",
+                                              "kernel": "exp_abs:0.5", "launch": "CUDA graph replay"}})
     elif args.workload == "serve":
         from paper_2602_14016_gb300 import serve
 
@@ -506,7 +511,7 @@ def main():
     ap.add_argument("--roofline-evals", type=int, default=1)
     ap.add_argument("--no-graphs", dest="graphs", action="store_false")
     ap.add_argument("--tune-steps", type=int, default=8, help="RK steps per plan variant in the autotuner (0: off)")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "autograd", "serve"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "autograd", "serve", "grids"],
                     help="sweep: the headline workload above; the others print their own line")
     ap.add_argument("--ens256", type=int, default=256)
     ap.add_argument("--ens512", type=int, default=64)

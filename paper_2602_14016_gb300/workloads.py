@@ -164,6 +164,46 @@ def autograd_check(api, torch, n=512, nsteps=4000, dt=1e-3, nu=1 / 200, nf=4, ck
 
 
 # ---------------------------------------------------------------------------
+# Throughput per grid size
+# ---------------------------------------------------------------------------
+
+def grid_sweep(api, torch, grids=(64, 128, 256, 512, 1024), batches=(1, 8), steps=200, repeats=3, tune_steps=4):
+    """Cost-and-gradient throughput (gridpoint-steps/s, graph replay) of a
+    decaying-turbulence window per grid size and batch, each context on the
+    plan its autotuner keeps.  Inputs: seeded unit-energy fields, probe data
+    of a second seed, 8x8 probes every 10 steps."""
+    dts = {64: 5e-3, 128: 4e-3, 256: 2e-3, 512: 1e-3, 1024: 5e-4}
+    rows = []
+    for n in grids:
+        for B in batches:
+            cfg = api.Config(n=n, nsteps=steps, dt=dts[n], nu=1e-3, px=8, every=10,
+                             kernels=[api.KernelSpec("exp_abs", 0.5)] * B)
+            ctx = api.Context(cfg)
+            plan, plan_ms = ctx.autotune(tune_steps) if tune_steps > 0 else (ctx.plan, None)
+            w = torch.from_numpy(np.stack([synthetic.random_vorticity_hat(n, 1000 + b) for b in range(B)])).cuda()
+            _, m = ctx.forward(ctx.control_from_omega(w))
+            ctx.set_observations(m)
+            s = ctx.control_from_omega(
+                torch.from_numpy(np.stack([synthetic.random_vorticity_hat(n, 2000 + b) for b in range(B)])).cuda())
+            ctx.set_graphs(True)
+            for _ in range(2):
+                ctx.cost_grad(s)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(repeats):
+                ctx.cost_grad(s)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / repeats
+            rows.append({"n": n, "batch": B, "steps": steps, "ms_per_evaluation": ms,
+                         "gridpoint_steps_per_s": B * n * n * steps / (ms / 1e3), "fft_plan": plan,
+                         "plan_ms_per_step": plan_ms})
+            ctx.close()
+    return rows
+
+
+# ---------------------------------------------------------------------------
 # Serving
 # ---------------------------------------------------------------------------
 
