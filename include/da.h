@@ -54,7 +54,8 @@ typedef enum {
   DA_EINVAL = 1,     /* invalid argument or unsupported size */
   DA_ENOMEM = 2,     /* device allocation failed (trajectory too large, ...) */
   DA_ECUDA = 3,      /* a CUDA call failed; context state is undefined */
-  DA_ETIMEOUT = 4,   /* a bounded device wait gave up */
+  DA_ETIMEOUT = 4,   /* reserved: a bounded device wait gave up (no call of this version
+                        waits on the device) */
   DA_EDIVERGED = 5,  /* non-finite cost or gradient */
   DA_ENOTCONV = 6    /* the optimiser stopped on a line-search failure */
 } da_status;
