@@ -13,7 +13,9 @@ are numpy complex128 of shape (n, n//2 + 1) holding the half spectrum
 
 Parity status: all wrapped functions are pinned by ``tests/test_oracle_*``
 (brute-force DFT, closed forms, Taylor-Green decay, laminar Kolmogorov,
-conservation, dot-product tests, finite differences).  The L-BFGS driver in
+conservation, dot-product tests, finite differences; the control multiplier
+|k| W^{1/2} of every kernel family by exact values at special parameters and
+by the families' semigroup and power identities).  The L-BFGS driver in
 ``oracle/lbfgs.py`` is pinned on the toy problem of Sec. II.C and on
 quadratics; beyond that, full assimilation trajectories are compared only on
 their first iterations.

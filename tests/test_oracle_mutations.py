@@ -4,11 +4,14 @@ Each case plants one mistake (a dropped term, a wrong sign, a wrong index or
 coefficient, a missing conjugation) in a copy of the oracle's C source,
 compiles it, and checks that at least one pin of the battery below fails,
 while the unmodified source passes all of them."""
+import math
+
 import numpy as np
 import pytest
 
 from conftest import dot, phys, rel
 from paper_2602_14016_gb300 import synthetic
+from test_oracle_kernel_w import mode_multiplier
 
 
 def _grid(n):
@@ -111,6 +114,22 @@ def battery(orc):
         fd = (orc.cost(Q, s + 1e-4 * d, m) - orc.cost(Q, s - 1e-4 * d, m)) / 2e-4
         return abs(fd - np.sum(g * d)) < 1e-7 * abs(fd)
 
+    def kernel_values():
+        # m(k) = |k| W^{1/2} at modes where special parameters fix exact values
+        KX, KY = synthetic.wavenumbers(n)
+        table = 4.0 ** (-np.abs(KX)) * 9.0 ** (-np.abs(KY))
+        cases = [("exp_abs", math.log(4.0), 1e-2, None, [(1, 0, 0.5), (3, 4, 5 / 32)]),
+                 ("frac", 0.5, 1e-2, None, [(0, 4, 2.0), (3, 4, math.sqrt(5.0))]),
+                 ("frac", 1.5, 1e-2, None, [(0, 4, 0.5)]),
+                 ("exp_sq", 100 * math.log(2.0), 1e-2, None, [(1, 1, math.sqrt(2.0) / 2), (0, 2, 0.5)]),
+                 ("table", 0.0, 1e-2, table, [(0, 1, 1 / 3), (4, -3, 5 / 432)])]
+        for kernel, kp, nu, tab, vals in cases:
+            Q = orc.Problem(n=n, nsteps=1, dt=1e-3, nu=nu, px=4, every=1, kernel=kernel, kparam=kp, ktable=tab)
+            for kx, ky, m in vals:
+                if abs(mode_multiplier(orc, Q, kx, ky) - m) > 4e-15 * m:
+                    return False
+        return True
+
     def gradient_fd():
         truth = orc.control_from_omega(P, synthetic.random_vorticity_hat(n, 20) * 2)
         _, m = orc.forward(P, truth)
@@ -124,7 +143,7 @@ def battery(orc):
                      ("kolmogorov", kolmogorov), ("conservation", conservation), ("rhs_dot", rhs_dot),
                      ("rhs_tangent", rhs_tangent), ("step", step_dot), ("obs_transpose", obs_transpose),
                      ("vorticity_control", vorticity_control), ("control_transpose", control_transpose),
-                     ("gradient_fd", gradient_fd), ("sobolev_fd", sobolev_fd)]:
+                     ("gradient_fd", gradient_fd), ("sobolev_fd", sobolev_fd), ("kernel_values", kernel_values)]:
         check(name, fn)
     return failed
 
@@ -146,6 +165,11 @@ MUTATIONS = [
      "o[i] = in_R(kx, ky, n) ? (acc[i] + c->nu * k2 * mu[i]) : 0;"),
     ("dealias_cut", "return abs(kx) <= K && abs(ky) <= K;", "return abs(kx) <= K + 1 && abs(ky) <= K + 1;"),
     ("nonlinear_term_dropped", "nl[i] = g.u[i] * g.wx[i] + g.v[i] * g.wy[i];", "nl[i] = g.u[i] * g.wx[i];"),
+    ("exp_abs_squared_exponent", "case 1: return exp(-c->kparam * k);", "case 1: return exp(-c->kparam * k2);"),
+    ("exp_sq_drops_nu", "case 3: return exp(-c->nu * c->kparam * k2);", "case 3: return exp(-c->kparam * k2);"),
+    ("W_in_place_of_sqrt_W", "return k * sqrt(kernel_W(c, kx, ky, q, p));", "return k * kernel_W(c, kx, ky, q, p);"),
+    ("frac_half_exponent", "case 2: return pow(k, -2.0 * c->kparam);", "case 2: return pow(k, -c->kparam);"),
+    ("table_transposed", "case 4: return c->ktable[q * nh(c->n) + p];", "case 4: return c->ktable[p * nh(c->n) + q];"),
     ("sobolev_gradient_sign", "for (int i = 0; i < nn; ++i) lam[i] += c->sobolev * t2[i];",
      "for (int i = 0; i < nn; ++i) lam[i] -= c->sobolev * t2[i];"),
 ]
