@@ -45,9 +45,50 @@ WORKLOAD_NAME = "kolmogorov-256sq-2000steps-16x16probes-7kernel-sweep"
 METRIC = "fwd+adjoint gridpoint-steps/s FP64"
 UNIT = "gridpoint-steps/s"
 
-# FP64 peak for an ALU-bound kernel: 152 SMs x 2 DFMA/clk/SM (measured by a
-# DFMA throughput probe on this GPU) x 2 flop x 2.07 GHz maximum SM clock.
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+PROBE_KINDS = {0: "dfma_reg_const", 1: "dfma_3reg", 2: "dadd", 3: "dmul"}
+
+
+def sm_max_mhz() -> tuple:
+    """Maximum SM clock: MEASURED_PEAKS.json, else the recipe's 2070 MHz."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+    except (OSError, KeyError, ValueError):
+        return 2070.0, "recipe maximum SM clock"
+
+
+def fp64_probe(kinds=(0, 1, 2, 3), iters: int = 100000) -> dict:
+    """Runs da_fp64_probe (csrc/fp64_probe.cu) for each kind on the current
+    device: {name: {gflops, ops_per_clk_per_sm, sm_mhz}}."""
+    import ctypes
+
+    import torch
+
+    from paper_2602_14016_gb300 import _native as NN
+
+    lib = NN.load()
+    out = {}
+    for k in kinds:
+        g, r, mhz = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        st = lib.da_fp64_probe(k, iters, ctypes.byref(g), ctypes.byref(r), ctypes.byref(mhz),
+                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if st != NN.DA_OK:
+            raise RuntimeError(f"da_fp64_probe({k}) returned {st}")
+        out[PROBE_KINDS[k]] = {"gflops": g.value, "ops_per_clk_per_sm": r.value, "sm_mhz": mhz.value}
+    return out
+
+
+def fp64_peak(probe: dict, sms: int) -> dict:
+    """Roofline denominator of the FP64-bound pass kernels, derived from unit
+    counts and clocks: SMs x DFMA per clock per SM x 2 flop x maximum SM clock.
+    The DFMA rate per SM is the probe's best DFMA rate rounded to a whole
+    number of operations per clock (the pipe issues whole operations)."""
+    best = max(probe[k]["ops_per_clk_per_sm"] for k in ("dfma_reg_const", "dfma_3reg") if k in probe)
+    units = max(1, round(best))
+    mhz, src = sm_max_mhz()
+    return {"gflops": sms * units * 2 * mhz / 1e3, "sms": sms, "dfma_per_clk_per_sm": units,
+            "probe_best_dfma_per_clk_per_sm": best, "sm_max_mhz": mhz, "clock_source": src,
+            "source": "derived: SMs x DFMA/clk/SM (da_fp64_probe, this run) x 2 flop x max SM clock"}
 
 # DRAM bytes (read + write) per launch of each pass kernel at this workload
 # (256^2, batch 7), from one ncu capture of the same launch configuration on
@@ -345,6 +386,9 @@ def run_gpu(args):
     pf = pass_flops(n, B)[dom]
     avg_ms = dom_ms / max(dom_n, 1)
     achieved = pf / (avg_ms / 1e3) / 1e9
+    probe = fp64_probe((0, 1), iters=50000)
+    peak = fp64_peak(probe, torch.cuda.get_device_properties(device).multi_processor_count)
+    peak_gflops = peak["gflops"]
     traffic = TRAFFIC.get(dom) if (TRAFFIC.get("src_hash") == src_hash() and n == 256 and B == 7) else None
     cpu = cpu_baseline(args) if args.cpu_baseline else None
     line = {
@@ -368,13 +412,13 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(s_host.numel() * 8),
                 "d2h_bytes_per_step": int(J_host.numel() * 8 + g_host.numel() * 8)},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
-                     "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_gflops,
+                     "unit": "GFLOP/s", "frac": achieved / peak_gflops, "traffic": traffic,
                      "flops_per_launch": pf, "avg_launch_ms": avg_ms, "launches_timed": dom_n,
                      "timed_in": "roofline pass of the same workload, direct launches, CUDA events per launch",
                      "roofline_pass_ms_per_step": roof_pass_ms,
                      "class_ms_warmup": {k: v[0] for k, v in class_ms.items()},
-                     "hbm": hbm_fraction(traffic, avg_ms)},
+                     "hbm": hbm_fraction(traffic, avg_ms), "peak_derivation": peak, "fp64_probe": probe},
         "flops_per_gridpoint_step": flops_per_gridpoint_step(n),
         "achieved_gflops_step": value * flops_per_gridpoint_step(n) / 1e9,
         "cpu_baseline": cpu,
@@ -476,6 +520,14 @@ def run_workload(args):
         line.update({"metric": "fwd+adjoint gridpoint-steps/s FP64 per grid size and batch", "unit": UNIT,
                      "rows": rows, "config": {"flow": "decaying, nu 1e-3", "probes": "8x8 every 10 steps",
                                               "kernel": "exp_abs:0.5", "launch": "CUDA graph replay"}})
+    elif args.workload == "fp64peak":
+        with ClockSampler(0) as clk:
+            probe = fp64_probe(iters=args.probe_iters)
+        peak = fp64_peak(probe, torch.cuda.get_device_properties(0).multi_processor_count)
+        line.update({"metric": "FP64 throughput per operation kind (GFLOP/s; DFMA counts 2)", "unit": "GFLOP/s",
+                     "kinds": probe, "roofline_peak": peak, "clocks": clk.summary(),
+                     "config": {"probe": "8 independent chains per thread, 4 CTAs x 256 threads per SM",
+                                "iters": args.probe_iters}})
     elif args.workload == "serve":
         from paper_2602_14016_gb300 import serve
 
@@ -511,7 +563,9 @@ def main():
     ap.add_argument("--roofline-evals", type=int, default=1)
     ap.add_argument("--no-graphs", dest="graphs", action="store_false")
     ap.add_argument("--tune-steps", type=int, default=8, help="RK steps per plan variant in the autotuner (0: off)")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "autograd", "serve", "grids"],
+    ap.add_argument("--probe-iters", type=int, default=100000, help="fp64peak: loop rounds per thread")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "autograd", "serve", "grids",
+                                                            "fp64peak"],
                     help="sweep: the headline workload above; the others print their own line")
     ap.add_argument("--ens256", type=int, default=256)
     ap.add_argument("--ens512", type=int, default=64)

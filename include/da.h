@@ -121,11 +121,20 @@ typedef struct {
   int max_ls_evals;  /* cost-gradient evaluations per line search [20] */
 } da_lbfgs_opts;
 
-/* Create a context.  `kernels` points to grid->batch descriptors (one per
- * member).  Allocates every device buffer the window needs, so later calls
- * allocate nothing.  Returns DA_EINVAL for unsupported sizes (message in
- * *out's last error if *out was created, else via da_last_error(NULL)),
- * DA_ENOMEM if the trajectory does not fit. */
+/* Create a context for a batch of assimilation windows of the model of
+ * Eq. (1) (Eq. 24 with Kolmogorov forcing), the probes and times of Eq. (3)
+ * and one preconditioning kernel W per member (Sec. II.C, III.B).
+ * `kernels` points to grid->batch descriptors (one per member).  Allocates
+ * the device buffers of the forward solve, the stored trajectory and the
+ * adjoint sweep, so that da_forward, da_cost_grad, da_vjp,
+ * da_adjoint_terminal, the control maps and da_last_adjoint allocate
+ * nothing; da_assimilate, da_set_sobolev, da_set_graphs and
+ * da_adjoint_spectra allocate their own buffers on first use (stated at
+ * each).  Returns DA_EINVAL for unsupported sizes or a kernel whose W is not
+ * finite and non-negative on the retained set (message via
+ * da_last_error(NULL)), DA_ENOMEM if a device allocation (usually the
+ * trajectory, 64 n^2 bytes per step per member) fails; on failure *out is
+ * NULL and nothing stays allocated. */
 da_status da_create(da_ctx** out, const da_grid* grid, double nu, const da_forcing* forcing,
                     const da_obs_operator* obs, const da_kernel* kernels);
 
@@ -136,18 +145,26 @@ da_status da_create(da_ctx** out, const da_grid* grid, double nu, const da_forci
  * spectrum per member on the first non-zero lambda. */
 da_status da_set_sobolev(da_ctx* ctx, double lambda);
 
-/* Observations m, DEVICE pointer [batch][nt][px*py][2] with nt the number
- * of observation times; copied into the context on `stream`. */
+/* Observations m_ij of Eq. (3): DEVICE (or host) pointer
+ * [batch][nt][px*py][2] (u, v per probe) with nt = da_num_obs_times(ctx);
+ * copied into the context on `stream` (the caller's buffer may be reused once
+ * the stream has passed the copy). */
 da_status da_set_observations(da_ctx* ctx, const double* m, void* stream);
 
-/* Forward solve from controls s [batch][n][n].  omegaT (nullable) receives
- * the final vorticity half spectrum [batch][n][n/2+1] complex; obs
- * (nullable) the model observations [batch][nt][px*py][2]. */
+/* Forward solve of Eq. (1)/(24) over the window from the initial vorticity
+ * w0_hat = P |k| W^{1/2} DFT(s) (Eq. 18-19).  s: DEVICE [batch][n][n];
+ * omegaT (nullable): DEVICE [batch][n][n/2+1] complex, the final vorticity
+ * half spectrum; obs (nullable): DEVICE [batch][nt][px*py][2], the model
+ * velocities at the probes and times of Eq. (3).  Keeps the trajectory for
+ * da_vjp when the context stores one. */
 da_status da_forward(da_ctx* ctx, const double* s, double* omegaT, double* obs, void* stream);
 
-/* Cost and gradient: J [batch] (HOST or DEVICE pointer; a host pointer makes
- * the call wait for the stream) and grad_s [batch][n][n] (device, may be
- * NULL).  Uses the observations of da_set_observations. */
+/* Cost J of Eq. (2)-(3) and its gradient with respect to the control,
+ * grad_s J = IDFT(P |k| W^{1/2} DFT(grad_{w0} J)) (Eq. 19), grad_{w0} J from
+ * the discrete adjoint of the forward scheme (Eq. 11-12).  s: DEVICE
+ * [batch][n][n]; J: [batch], HOST or DEVICE pointer (a host pointer makes
+ * the call wait for the stream); grad_s: DEVICE [batch][n][n] (nullable).
+ * Uses the observations of da_set_observations (DA_EINVAL without them). */
 da_status da_cost_grad(da_ctx* ctx, const double* s, double* J, double* grad_s, void* stream);
 
 /* Vector-Jacobian product of the last da_forward on this context (which
@@ -167,7 +184,9 @@ da_status da_vjp(da_ctx* ctx, const double* dobs, const double* dwT, double* gra
  * events; the control is copied into and the gradient out of internal
  * buffers.  For small grids this removes the per-launch host cost.  The
  * capture is redone after da_set_sobolev; kernel timing (da_time_kernels)
- * bypasses the graph.  The first call must not itself be inside a capture. */
+ * bypasses the graph.  The first call must not itself be inside a capture.
+ * The first enabling call allocates the two internal buffers (2 batch n^2
+ * doubles), a stream and two events. */
 da_status da_set_graphs(da_ctx* ctx, int enable);
 
 /* FFT plan variants (no counterpart in the paper, whose solver is not
@@ -224,25 +243,45 @@ da_status da_adjoint_terminal(da_ctx* ctx, const double* s, const double* lamT, 
  * [batch][nsteps/save_every + 1][nshell] per member (nullable); mean: DEVICE
  * [nsteps/save_every + 1][nshell] of the ensemble-mean adjoint over the
  * batch (nullable).  nshell = da_num_shells(ctx).  Reductions run in a fixed
- * order.  save_every must divide nsteps. */
+ * order.  save_every must divide nsteps.  The first call allocates the shell
+ * lists (one int and one double per retained mode) and, with `member`, a
+ * [batch][nshell] scratch. */
 da_status da_adjoint_spectra(da_ctx* ctx, const double* s, const double* lamT, int save_every, double* member,
                              double* mean, void* stream);
 
 /* Number of wavenumber shells of da_adjoint_spectra: floor(sqrt(2) K) + 1. */
 int da_num_shells(const da_ctx* ctx);
 
-/* L-BFGS on s (in/out, [batch][n][n]) for up to max_iter iterations, each
- * member independently.  J_hist: HOST [batch][max_iter+1], the cost at the
- * start and after every iteration (entries past a member's last iteration
- * repeat its final cost); iters_done: HOST [batch].  Returns DA_ENOTCONV if
- * some member stopped on a line-search failure, DA_EDIVERGED on a
- * non-finite cost.  opts may be NULL. */
+/* L-BFGS on the transformed control (Sec. II.C, Eq. 18-19: the paper's
+ * optimiser, run in the Euclidean metric of s) for up to max_iter
+ * iterations, each member independently; the members of the batch advance in
+ * lockstep and share every cost-and-gradient evaluation.
+ *   s: DEVICE [batch][n][n], in: first guesses; out: each member's last
+ *     accepted control (its first guess if it never accepted a step).
+ *   J_hist: HOST [batch][max_iter+1], the cost at the start and after every
+ *     iteration (entries past a member's last iteration repeat its final cost).
+ *   iters_done: HOST [batch], iterations each member completed.
+ *   member_status: HOST [batch] (nullable), per member DA_OK (converged or
+ *     max_iter reached), DA_ENOTCONV (line-search failure: the step-size
+ *     collapse of Sec. III.C-D) or DA_EDIVERGED (non-finite cost or
+ *     gradient); one member's failure leaves the others' results intact.
+ * Returns DA_EDIVERGED if some member diverged, else DA_ENOTCONV if some
+ * member's line search failed, else DA_OK; DA_EINVAL for bad arguments or
+ * opts->memory > 64.  opts may be NULL.  The first call on a context
+ * allocates the optimiser's device buffers ((2 memory + 7) n^2 doubles per
+ * member) and a small pinned host buffer.  The call waits for `stream` (the
+ * line search decides on the host): one host read per trial evaluation and
+ * two per iteration. */
 da_status da_assimilate(da_ctx* ctx, double* s, int max_iter, const da_lbfgs_opts* opts, double* J_hist,
-                        int* iters_done, void* stream);
+                        int* iters_done, int* member_status, void* stream);
 
-/* Control maps of member kernels: omega0 half spectrum [batch][n][n/2+1]
- * complex <-> s [batch][n][n].  da_omega_from_control applies P |k| W^{1/2};
- * da_control_from_omega its inverse on the retained set. */
+/* Control maps of the change of variables of Eq. (18)-(19), one kernel per
+ * member: omega0 DEVICE [batch][n][n/2+1] complex (half spectrum) <-> s
+ * DEVICE [batch][n][n].  da_omega_from_control writes
+ * w0_hat = P |k| W^{1/2} DFT(s) (zero mean, zero outside the retained set);
+ * da_control_from_omega is its right inverse on the retained set,
+ * s = IDFT(w0_hat / (|k| W^{1/2})) there and 0 elsewhere (modes where the
+ * multiplier underflows to 0 map to 0). */
 da_status da_omega_from_control(da_ctx* ctx, const double* s, double* omega0, void* stream);
 da_status da_control_from_omega(da_ctx* ctx, const double* omega0, double* s, void* stream);
 
@@ -268,6 +307,22 @@ da_status da_control_from_omega(da_ctx* ctx, const double* omega0, double* s, vo
  * later reads, so no state carries over between calls. */
 da_status da_omega_from_control_static(int n, double nu, const da_kernel* kernel, const double* s, double* omega0,
                                        void* stream, const char** message);
+
+/* FP64 throughput probe, a measurement utility (the paper has no
+ * counterpart): the pass kernels are bound by FP64 arithmetic, and this
+ * probe measures the pipe's issue rate that bounds them.  Runs 8 independent
+ * dependency chains per thread of one operation -- kind 0: DFMA with a
+ * register multiplicand and a constant addend; 1: DFMA with three register
+ * operands; 2: DADD; 3: DMUL -- on 4 CTAs of 256 threads per SM, iters x 32
+ * operations per thread, after a short warm-up launch, timed with CUDA
+ * events on `stream`.  gflops (HOST, required): FP64 flop/s / 1e9 (a DFMA
+ * counts 2); ops_per_clk_per_sm (HOST, nullable): operations per SM clock
+ * per SM; sm_mhz (HOST, nullable): the SM clock the probe ran at (clock64
+ * over %globaltimer on one thread).  Synchronous; allocates and frees a
+ * small device buffer (DA_ENOMEM if it cannot).  DA_EINVAL for kind outside
+ * [0, 3] or iters < 1. */
+da_status da_fp64_probe(int kind, int iters, double* gflops, double* ops_per_clk_per_sm, double* sm_mhz,
+                        void* stream);
 
 /* Number of observation times of the context (nt). */
 int da_num_obs_times(const da_ctx* ctx);

@@ -23,7 +23,7 @@ KERNEL_KINDS = {"identity": 0, "exp_abs": 1, "frac": 2, "exp_sq": 3, "table": 4}
 EXPORTS = ("da_create", "da_set_sobolev", "da_set_graphs", "da_plan_count", "da_get_plan", "da_set_plan", "da_autotune",
            "da_set_observations", "da_forward", "da_cost_grad", "da_vjp", "da_last_adjoint",
            "da_adjoint_terminal", "da_adjoint_spectra", "da_num_shells", "da_assimilate", "da_omega_from_control", "da_control_from_omega",
-           "da_omega_from_control_static", "da_num_obs_times", "da_device_bytes", "da_launch_count",
+           "da_omega_from_control_static", "da_fp64_probe", "da_num_obs_times", "da_device_bytes", "da_launch_count",
            "da_time_kernels", "da_kernel_time", "da_last_error", "da_destroy")
 
 
@@ -89,11 +89,12 @@ def load(path: str = LIB_PATH):
             "da_adjoint_terminal": (I, [C, P, P, P, P]),
             "da_adjoint_spectra": (I, [C, P, P, I, P, P, P]),
             "da_num_shells": (I, [C]),
-            "da_assimilate": (I, [C, P, I, ctypes.POINTER(LbfgsOpts), P, P, P]),
+            "da_assimilate": (I, [C, P, I, ctypes.POINTER(LbfgsOpts), P, P, P, P]),
             "da_omega_from_control": (I, [C, P, P, P]),
             "da_control_from_omega": (I, [C, P, P, P]),
             "da_omega_from_control_static": (I, [I, D, ctypes.POINTER(Kernel), P, P, P,
                                                  ctypes.POINTER(ctypes.c_char_p)]),
+            "da_fp64_probe": (I, [I, I, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), P]),
             "da_num_obs_times": (I, [C]),
             "da_device_bytes": (ctypes.c_ulonglong, [C]),
             "da_launch_count": (ctypes.c_ulonglong, [C]),

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 from dataclasses import dataclass, field
+from typing import NamedTuple
 
 import torch
 
@@ -60,6 +61,13 @@ def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p | None:
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("tensors must be contiguous CUDA tensors")
     return ctypes.c_void_p(t.data_ptr())
+
+
+class AssimResult(NamedTuple):
+    J_hist: "object"  # numpy [B, max_iter+1]
+    iters: "object"  # numpy int32 [B]
+    status: int  # status of the call (worst over members)
+    member_status: "object"  # numpy int32 [B]
 
 
 class Context:
@@ -197,19 +205,26 @@ class Context:
         return member, mean
 
     def assimilate(self, s: torch.Tensor, max_iter: int, memory: int = 10, c1: float = 1e-4, c2: float = 0.9,
-                   gtol_rel: float = 1e-10, max_ls_evals: int = 20, stream=None, raise_on_notconv: bool = False):
-        """L-BFGS on s (updated in place).  Returns (J_hist [B, max_iter+1], iters [B], status)."""
+                   gtol_rel: float = 1e-10, max_ls_evals: int = 20, stream=None, raise_on_notconv: bool = False,
+                   raise_on_diverged: bool = False):
+        """L-BFGS on s (updated in place).  Returns an AssimResult: J_hist
+        [B, max_iter+1], iters [B], the call's status and member_status [B]
+        (DA_OK, DA_ENOTCONV or DA_EDIVERGED per member).  A member that
+        diverges or whose line search fails does not discard the others'
+        results; raise_on_* turn those statuses into a DAError."""
         import numpy as np
 
         assert s.is_contiguous() and s.dtype == torch.float64
         J = np.zeros((self.cfg.batch, max_iter + 1), np.float64)
         it = np.zeros(self.cfg.batch, np.int32)
+        ms = np.zeros(self.cfg.batch, np.int32)
         o = N.LbfgsOpts(memory, c1, c2, gtol_rel, max_ls_evals)
         st = self.lib.da_assimilate(self.ctx, _ptr(s), max_iter, ctypes.byref(o), J.ctypes.data, it.ctypes.data,
-                                    _stream(stream))
-        if st not in (N.DA_OK, N.DA_ENOTCONV) or (raise_on_notconv and st == N.DA_ENOTCONV):
+                                    ms.ctypes.data, _stream(stream))
+        if (st not in (N.DA_OK, N.DA_ENOTCONV, N.DA_EDIVERGED) or (raise_on_notconv and st == N.DA_ENOTCONV)
+                or (raise_on_diverged and st == N.DA_EDIVERGED)):
             self._check(st)
-        return J, it, st
+        return AssimResult(J, it, st, ms)
 
     def omega_from_control(self, s: torch.Tensor, stream=None):
         w = self._spec()

@@ -1,23 +1,53 @@
-// blas.cuh -- per-member vector kernels of the optimiser.  Every member of a
-// batch has its own vectors, addressed through device arrays of B pointers
-// (a NULL pointer skips that member).  Reductions run in a fixed order, so
-// dot products are bitwise reproducible.
+// blas.cuh -- per-member vector kernels of the optimiser (L-BFGS, Sec. II.C).
+//
+// Every member of a batch owns a set of vectors of `len` doubles in one bank
+// buffer: bank k of member b starts at V + (k * B + b) * len.  Banks:
+// x, g, d (search direction), xt, gt (trial point and its gradient), then
+// the S slots and the Y slots of the pair ring.  One CTA serves one member
+// (blockIdx.x = member), so every reduction is a CTA tree reduction in a
+// fixed order: results are bitwise reproducible, and the two-loop recursion
+// runs as one launch with all of its scalars on the device.
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
 
 namespace da {
 
-constexpr int kDotChunk = 8192;
-inline int dot_chunks(size_t len) { return (int)((len + kDotChunk - 1) / kDotChunk); }
+enum : int { BANK_X = 0, BANK_G = 1, BANK_D = 2, BANK_XT = 3, BANK_GT = 4, BANK_S0 = 5 };
 
-// part[b][chunk] = sum over the chunk of a_b[i] * c_b[i].  grid (chunks, B), block 256.
-__global__ void k_dot_partial(const double* const* __restrict__ A, const double* const* __restrict__ C,
-                              double* __restrict__ part, size_t len);
-// out[b] = sum over chunks of part[b][chunk], in chunk order.  grid B, block 256.
-__global__ void k_dot_final(const double* __restrict__ part, double* __restrict__ out, int chunks);
-// y_b = alpha_b x_b + beta_b y_b.  grid (ceil(len/1024), B), block 256.
-__global__ void k_axpby(const double* const* __restrict__ X, double* const* __restrict__ Y,
-                        const double* __restrict__ alpha, const double* __restrict__ beta, size_t len);
+// Device scalars per member, [B][SC_COUNT].
+enum : int { SC_J = 0, SC_GG = 1, SC_GD = 2, SC_DG = 3, SC_SY = 4, SC_YY = 5, SC_COUNT = 6 };
+
+constexpr int kBlasThreads = 512;
+
+// Per-call arguments uploaded by the host (one small copy per phase).
+struct LbfgsArgs {
+  double* V;            // banks
+  size_t len;           // doubles per vector
+  int B, slots;         // members; S slots at BANK_S0 + t, Y slots at BANK_S0 + slots + t
+  int mem;              // pair capacity (slots - 1)
+  double* scal;         // [B][SC_COUNT]
+  const int* mask;      // [B] member takes part in this launch
+  const int* cnt;       // [B] pairs held (two-loop)
+  const int* pslot;     // [B][mem] slot of each pair, oldest first
+  const double* prho;   // [B][mem] 1 / (s . y) of each pair
+  const double* stp;    // [B] trial step
+  const int* aslot;     // [B] slot that receives an accepted pair
+};
+
+// d = -H g by the two-loop recursion with H0 = (s.y / y.y) I from the
+// newest pair, then scal[GD] = g . d.  grid B, block kBlasThreads.
+__global__ void k_two_loop(LbfgsArgs a);
+// d = -g for masked members.  grid (chunks, B).
+__global__ void k_neg_grad(LbfgsArgs a);
+// xt = x + stp d for masked members, xt = x for the others.  grid (chunks, B).
+__global__ void k_trial(LbfgsArgs a);
+// scal[DG] = gt . d for masked members.  grid B.
+__global__ void k_dot_gt_d(LbfgsArgs a);
+// Masked members accept their trial: S[aslot] = xt - x, Y[aslot] = gt - g,
+// scal[SY], scal[YY], x = xt, g = gt.  grid B.
+__global__ void k_accept(LbfgsArgs a);
+// scal[GG] = g . g for every member.  grid B.
+__global__ void k_gnorm2(LbfgsArgs a);
 
 }  // namespace da

@@ -41,10 +41,13 @@ struct da_ctx {
   double *shell_wgt = nullptr, *shell_scratch = nullptr;
   double2* w0 = nullptr;  // compact initial state kept for that term
   std::string err;
-  // optimiser buffers (allocated on first da_assimilate)
-  double *x = nullptr, *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr, *S = nullptr, *Y = nullptr;
-  double *part = nullptr, *dots = nullptr, *scal = nullptr;
-  void** ptrs = nullptr;
+  // optimiser buffers (allocated on the first da_assimilate; blas.cuh)
+  double* lb_V = nullptr;      // vector banks [5 + 2 (mem + 1)][B][n^2]
+  double* lb_scal = nullptr;   // device scalars [B][SC_COUNT]
+  double* lb_J = nullptr;      // costs [B]
+  int* lb_iargs = nullptr;     // argument tables of the vector kernels
+  double* lb_dargs = nullptr;
+  double* lb_host = nullptr;   // pinned mirror of lb_scal and lb_J
   int mem = 0;
   // CUDA-graph replay of da_cost_grad
   bool use_graph = false;

@@ -223,6 +223,7 @@ extern "C" void da_destroy(da_ctx* c) {
   if (c->gstream) cudaStreamDestroy(c->gstream);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
+  if (c->lb_host) cudaFreeHost(c->lb_host);
   delete c;
 }
 

@@ -14,73 +14,110 @@
 // re-evaluates its accepted point, which changes nothing.  Each member keeps
 // a ring of memory+1 vector slots for its (s, y) pairs, so a new pair can be
 // formed and tested before the oldest one is dropped.
+//
+// The vectors and every scalar the recursion needs stay on the device: the
+// two-loop recursion is one launch, and the host reads scalars only where
+// its own decisions need them -- g.d after the recursion (descent test and
+// line-search start), the cost and phi'(stp) after each trial evaluation,
+// and s.y, y.y and |g| once per iteration (pair test, convergence test).
 // ---------------------------------------------------------------------------
 
 namespace {
 
-struct Vec {
-  da_ctx* c;
-  cudaStream_t st;
-  size_t len;
-
-  // out[b] = a_b . x_b (NULL pointer: 0)
-  da_status dot(const std::vector<const double*>& a, const std::vector<const double*>& x, std::vector<double>& out) {
-    const int B = c->B;
-    std::vector<const double*> ptrs(2 * B);
-    for (int b = 0; b < B; ++b) {
-      ptrs[b] = a[b];
-      ptrs[B + b] = x[b];
-    }
-    DA_TRY_CUDA(c, cudaMemcpyAsync(c->ptrs, ptrs.data(), 2 * B * sizeof(void*), cudaMemcpyHostToDevice, st));
-    const int chunks = da::dot_chunks(len);
-    da::k_dot_partial<<<dim3(chunks, B), 256, 0, st>>>((const double* const*)c->ptrs,
-                                                        (const double* const*)c->ptrs + B, c->part, len);
-    da::k_dot_final<<<B, 256, 0, st>>>(c->part, c->dots, chunks);
-    da_status r = check_launch(c, 2);
-    if (r) return r;
-    out.assign(B, 0.0);
-    DA_TRY_CUDA(c, cudaMemcpyAsync(out.data(), c->dots, B * sizeof(double), cudaMemcpyDeviceToHost, st));
-    DA_TRY_CUDA(c, cudaStreamSynchronize(st));
-    return DA_OK;
-  }
-
-  // y_b = alpha_b x_b + beta_b y_b (NULL pointer: member untouched)
-  da_status axpby(const std::vector<double>& alpha, const std::vector<const double*>& x,
-                  const std::vector<double>& beta, const std::vector<double*>& y) {
-    const int B = c->B;
-    std::vector<const void*> ptrs(2 * B);
-    std::vector<double> ab(2 * B);
-    for (int b = 0; b < B; ++b) {
-      ptrs[b] = x[b];
-      ptrs[B + b] = y[b];
-      ab[b] = alpha[b];
-      ab[B + b] = beta[b];
-    }
-    DA_TRY_CUDA(c, cudaMemcpyAsync(c->ptrs, ptrs.data(), 2 * B * sizeof(void*), cudaMemcpyHostToDevice, st));
-    DA_TRY_CUDA(c, cudaMemcpyAsync(c->scal, ab.data(), 2 * B * sizeof(double), cudaMemcpyHostToDevice, st));
-    da::k_axpby<<<dim3((unsigned)((len + 1023) / 1024), B), 256, 0, st>>>(
-        (const double* const*)c->ptrs, (double* const*)c->ptrs + B, c->scal, c->scal + B, len);
-    da_status r = check_launch(c);
-    if (r) return r;
-    DA_TRY_CUDA(c, cudaStreamSynchronize(st));  // host arrays must outlive the copies
-    return DA_OK;
-  }
-
-  double* member(double* base, int b) const { return base + (size_t)b * len; }
-};
+constexpr int kMaxMemory = 64;  // pairs; the recursion keeps its alphas in shared memory
 
 struct Member {
-  std::vector<int> pairs;    // slot indices, oldest first (at most `memory`)
-  std::vector<double> rho;   // 1 / (s . y) per pair
+  std::vector<int> pairs;   // slot indices, oldest first (at most `memory`)
+  std::vector<double> rho;  // 1 / (s . y) per pair
   double f = 0, gnorm = 0, g0norm = 0;
-  int state = 0;             // 0 active, 1 converged, 2 line-search failure, 3 diverged
+  int state = 0;            // 0 active, 1 converged, 2 line-search failure, 3 diverged
   int iters = 0;
+  int pending = -1;         // slot of a pair accepted in this iteration, tested at its end
 };
+
+// Per-call argument tables of the vector kernels, staged on the host and
+// copied to the context's argument buffers (pageable host memory: the copy
+// returns once the runtime has staged the bytes, so the tables can be
+// rewritten right after).
+struct Args {
+  da_ctx* c;
+  cudaStream_t st;
+  int B, m;
+  std::vector<int> ints;        // mask [B], cnt [B], aslot [B], pslot [B][m]
+  std::vector<double> dbls;     // stp [B], prho [B][m]
+
+  Args(da_ctx* c_, cudaStream_t s, int B_, int m_) : c(c_), st(s), B(B_), m(m_) {
+    ints.assign((size_t)3 * B + (size_t)B * m, 0);
+    dbls.assign((size_t)B + (size_t)B * m, 0.0);
+  }
+  int* mask() { return ints.data(); }
+  int* cnt() { return ints.data() + B; }
+  int* aslot() { return ints.data() + 2 * B; }
+  int* pslot() { return ints.data() + 3 * B; }
+  double* stp() { return dbls.data(); }
+  double* prho() { return dbls.data() + B; }
+
+  da::LbfgsArgs dev() const {
+    da::LbfgsArgs a{};
+    a.V = c->lb_V;
+    a.len = (size_t)c->n * c->n;
+    a.B = B;
+    a.slots = m + 1;
+    a.mem = m;
+    a.scal = c->lb_scal;
+    a.mask = c->lb_iargs;
+    a.cnt = c->lb_iargs + B;
+    a.aslot = c->lb_iargs + 2 * B;
+    a.pslot = c->lb_iargs + 3 * B;
+    a.stp = c->lb_dargs;
+    a.prho = c->lb_dargs + B;
+    return a;
+  }
+  da_status upload() {
+    DA_TRY_CUDA(c, cudaMemcpyAsync(c->lb_iargs, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    DA_TRY_CUDA(c, cudaMemcpyAsync(c->lb_dargs, dbls.data(), dbls.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    return DA_OK;
+  }
+};
+
+// Waits for the stream and returns the device scalars and costs in the
+// context's pinned mirror: lb_host[b * SC_COUNT + k], costs after them.
+da_status read_scalars(da_ctx* c, cudaStream_t st) {
+  const int B = c->B;
+  DA_TRY_CUDA(c, cudaMemcpyAsync(c->lb_host, c->lb_scal, (size_t)B * da::SC_COUNT * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+  DA_TRY_CUDA(c, cudaMemcpyAsync(c->lb_host + (size_t)B * da::SC_COUNT, c->lb_J, B * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+  DA_TRY_CUDA(c, cudaStreamSynchronize(st));
+  return DA_OK;
+}
+
+da_status alloc_optimiser(da_ctx* c, int m) {
+  const size_t B = c->B, len = (size_t)c->n * c->n, slots = m + 1;
+  da_status r = DA_OK;
+  auto A = [&](da_status x) {
+    if (r == DA_OK) r = x;
+  };
+  A(dalloc(c, &c->lb_V, (da::BANK_S0 + 2 * slots) * B * len));
+  A(dalloc(c, &c->lb_scal, B * da::SC_COUNT));
+  A(dalloc(c, &c->lb_J, B));
+  A(dalloc(c, &c->lb_iargs, 3 * B + B * m));
+  A(dalloc(c, &c->lb_dargs, B + B * m));
+  if (r) return r;
+  void* h = nullptr;
+  if (cudaMallocHost(&h, B * (da::SC_COUNT + 1) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, DA_ENOMEM, "pinned host buffer of the optimiser");
+  }
+  c->lb_host = static_cast<double*>(h);
+  c->mem = m;
+  return DA_OK;
+}
 
 }  // namespace
 
 extern "C" da_status da_assimilate(da_ctx* c, double* s, int max_iter, const da_lbfgs_opts* opts, double* J_hist,
-                                   int* iters_done, void* stream) {
+                                   int* iters_done, int* member_status, void* stream) {
   if (!c || !s || !J_hist || !iters_done || max_iter < 0) return fail(c, DA_EINVAL, "bad arguments");
   if (!c->have_obs) return fail(c, DA_EINVAL, "no observations: call da_set_observations first");
   if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
@@ -93,46 +130,36 @@ extern "C" da_status da_assimilate(da_ctx* c, double* s, int max_iter, const da_
     if (opts->gtol_rel > 0) o.gtol_rel = opts->gtol_rel;
     if (opts->max_ls_evals > 0) o.max_ls_evals = opts->max_ls_evals;
   }
+  if (o.memory > kMaxMemory) return fail(c, DA_EINVAL, "memory must be at most 64 pairs");
   const int B = c->B, m = o.memory, slots = m + 1;
   const size_t len = (size_t)c->n * c->n;
   da_status r = DA_OK;
   if (c->mem != m) {
     if (c->mem) return fail(c, DA_EINVAL, "memory must stay the same across calls on one context");
-    auto A = [&](da_status x) {
-      if (r == DA_OK) r = x;
-    };
-    A(dalloc(c, &c->x, B * len));
-    A(dalloc(c, &c->g, B * len));
-    A(dalloc(c, &c->d, B * len));
-    A(dalloc(c, &c->xt, B * len));
-    A(dalloc(c, &c->gt, B * len));
-    A(dalloc(c, &c->S, (size_t)slots * B * len));
-    A(dalloc(c, &c->Y, (size_t)slots * B * len));
-    A(dalloc(c, &c->part, (size_t)B * da::dot_chunks(len)));
-    A(dalloc(c, &c->dots, (size_t)B));
-    A(dalloc(c, &c->scal, (size_t)2 * B));
-    A(dalloc<void*>(c, &c->ptrs, (size_t)2 * B));
-    if (r) return r;
-    c->mem = m;
+    if ((r = alloc_optimiser(c, m))) return r;
   }
-  Vec V{c, st, len};
-  auto Sslot = [&](int slot, int b) { return c->S + ((size_t)slot * B + b) * len; };
-  auto Yslot = [&](int slot, int b) { return c->Y + ((size_t)slot * B + b) * len; };
-  const std::vector<double> zeros(B, 0.0), ones(B, 1.0);
+  Args A(c, st, B, m);
+  const da::LbfgsArgs dv = A.dev();
+  double* X = c->lb_V + (size_t)da::BANK_X * B * len;
+  double* G = c->lb_V + (size_t)da::BANK_G * B * len;
+  double* XT = c->lb_V + (size_t)da::BANK_XT * B * len;
+  double* GT = c->lb_V + (size_t)da::BANK_GT * B * len;
+  const double* hs = c->lb_host;                       // [B][SC_COUNT]
+  const double* hJ = c->lb_host + (size_t)B * da::SC_COUNT;  // [B]
+  auto sc = [&](int b, int k) { return hs[(size_t)b * da::SC_COUNT + k]; };
+  const dim3 ew((unsigned)((len + 4095) / 4096), B);  // element-wise kernels: 4096 elements per CTA
   std::vector<Member> mb(B);
-  std::vector<double> f(B), tmp;
-  std::vector<const double*> pa(B), pb(B);
-  std::vector<double*> py(B);
 
-  DA_TRY_CUDA(c, cudaMemcpyAsync(c->x, s, B * len * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  if ((r = da_cost_grad(c, c->x, f.data(), c->g, st))) return r;
-  for (int b = 0; b < B; ++b) pa[b] = V.member(c->g, b);
-  if ((r = V.dot(pa, pa, tmp))) return r;
+  DA_TRY_CUDA(c, cudaMemcpyAsync(X, s, B * len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if ((r = da_cost_grad(c, X, c->lb_J, G, st))) return r;
+  da::k_gnorm2<<<B, da::kBlasThreads, 0, st>>>(dv);
+  if ((r = check_launch(c))) return r;
+  if ((r = read_scalars(c, st))) return r;
   for (int b = 0; b < B; ++b) {
-    mb[b].f = f[b];
-    mb[b].g0norm = mb[b].gnorm = std::sqrt(tmp[b]);
-    if (!std::isfinite(f[b]) || !std::isfinite(tmp[b])) mb[b].state = 3;
-    J_hist[(size_t)b * (max_iter + 1)] = f[b];
+    mb[b].f = hJ[b];
+    mb[b].g0norm = mb[b].gnorm = std::sqrt(sc(b, da::SC_GG));
+    if (!std::isfinite(hJ[b]) || !std::isfinite(sc(b, da::SC_GG))) mb[b].state = 3;
+    J_hist[(size_t)b * (max_iter + 1)] = hJ[b];
   }
 
   for (int it = 0; it < max_iter; ++it) {
@@ -144,91 +171,38 @@ extern "C" da_status da_assimilate(da_ctx* c, double* s, int max_iter, const da_
     if (!any) break;
     auto active = [&](int b) { return mb[b].state == 0; };
 
-    // d = -H g by the two-loop recursion (d carries -q)
+    // d = -H g by the two-loop recursion, one launch for every active member
     for (int b = 0; b < B; ++b) {
-      pa[b] = active(b) ? V.member(c->g, b) : nullptr;
-      py[b] = active(b) ? V.member(c->d, b) : nullptr;
+      A.mask()[b] = active(b);
+      const int cnt = active(b) ? (int)mb[b].pairs.size() : 0;
+      A.cnt()[b] = cnt;
+      for (int j = 0; j < cnt; ++j) {
+        A.pslot()[(size_t)b * m + j] = mb[b].pairs[j];
+        A.prho()[(size_t)b * m + j] = mb[b].rho[j];
+      }
     }
-    std::vector<double> minus(B, -1.0);
-    if ((r = V.axpby(minus, pa, zeros, py))) return r;
-    int hmax = 0;
-    for (int b = 0; b < B; ++b)
-      if (active(b)) hmax = std::max(hmax, (int)mb[b].pairs.size());
-    std::vector<std::vector<double>> alpha(B, std::vector<double>(hmax, 0.0));
-    for (int h = 0; h < hmax; ++h) {  // newest to oldest
-      for (int b = 0; b < B; ++b) {
-        const int cnt = (int)mb[b].pairs.size();
-        const bool use = active(b) && h < cnt;
-        pa[b] = use ? Sslot(mb[b].pairs[cnt - 1 - h], b) : nullptr;
-        pb[b] = use ? V.member(c->d, b) : nullptr;
-      }
-      if ((r = V.dot(pa, pb, tmp))) return r;
-      std::vector<double> al(B, 0.0);
-      for (int b = 0; b < B; ++b) {
-        const int cnt = (int)mb[b].pairs.size();
-        const bool use = active(b) && h < cnt;
-        if (use) al[b] = alpha[b][h] = -mb[b].rho[cnt - 1 - h] * tmp[b];  // rho s.q
-        pa[b] = use ? Yslot(mb[b].pairs[cnt - 1 - h], b) : nullptr;
-        py[b] = use ? V.member(c->d, b) : nullptr;
-      }
-      if ((r = V.axpby(al, pa, ones, py))) return r;  // q -= alpha y
-    }
-    if (hmax > 0) {  // H0 = (s.y / y.y) I from the newest pair
-      for (int b = 0; b < B; ++b) {
-        const bool use = active(b) && !mb[b].pairs.empty();
-        pa[b] = use ? Yslot(mb[b].pairs.back(), b) : nullptr;
-      }
-      if ((r = V.dot(pa, pa, tmp))) return r;
-      std::vector<double> gam(B, 1.0);
-      for (int b = 0; b < B; ++b) {
-        const bool use = active(b) && !mb[b].pairs.empty();
-        if (use) gam[b] = 1.0 / (mb[b].rho.back() * tmp[b]);
-        pa[b] = use ? V.member(c->d, b) : nullptr;
-        py[b] = use ? V.member(c->d, b) : nullptr;
-      }
-      if ((r = V.axpby(zeros, pa, gam, py))) return r;
-    }
-    for (int h = hmax - 1; h >= 0; --h) {  // oldest to newest
-      for (int b = 0; b < B; ++b) {
-        const int cnt = (int)mb[b].pairs.size();
-        const bool use = active(b) && h < cnt;
-        pa[b] = use ? Yslot(mb[b].pairs[cnt - 1 - h], b) : nullptr;
-        pb[b] = use ? V.member(c->d, b) : nullptr;
-      }
-      if ((r = V.dot(pa, pb, tmp))) return r;
-      std::vector<double> al(B, 0.0);
-      for (int b = 0; b < B; ++b) {
-        const int cnt = (int)mb[b].pairs.size();
-        const bool use = active(b) && h < cnt;
-        if (use) al[b] = -(alpha[b][h] - (-mb[b].rho[cnt - 1 - h] * tmp[b]));  // r += (alpha - beta) s
-        pa[b] = use ? Sslot(mb[b].pairs[cnt - 1 - h], b) : nullptr;
-        py[b] = use ? V.member(c->d, b) : nullptr;
-      }
-      if ((r = V.axpby(al, pa, ones, py))) return r;
-    }
+    if ((r = A.upload())) return r;
+    da::k_two_loop<<<B, da::kBlasThreads, 0, st>>>(dv);
+    if ((r = check_launch(c))) return r;
+    if ((r = read_scalars(c, st))) return r;
+    std::vector<double> gd(B, 0.0);
+    bool reset = false;
     for (int b = 0; b < B; ++b) {
-      pa[b] = active(b) ? V.member(c->g, b) : nullptr;
-      pb[b] = active(b) ? V.member(c->d, b) : nullptr;
-    }
-    std::vector<double> gd;
-    if ((r = V.dot(pa, pb, gd))) return r;
-    {
-      std::vector<double> al(B, 0.0);
-      bool reset = false;
-      for (int b = 0; b < B; ++b) {
-        pa[b] = nullptr;
-        py[b] = nullptr;
-        if (active(b) && !(gd[b] < 0.0)) {  // not a descent direction: restart from -g
-          mb[b].pairs.clear();
-          mb[b].rho.clear();
-          al[b] = -1.0;
-          pa[b] = V.member(c->g, b);
-          py[b] = V.member(c->d, b);
-          gd[b] = -mb[b].gnorm * mb[b].gnorm;
-          reset = true;
-        }
+      A.mask()[b] = 0;
+      if (!active(b)) continue;
+      gd[b] = sc(b, da::SC_GD);
+      if (!(gd[b] < 0.0)) {  // not a descent direction: restart from -g
+        mb[b].pairs.clear();
+        mb[b].rho.clear();
+        gd[b] = -mb[b].gnorm * mb[b].gnorm;
+        A.mask()[b] = 1;
+        reset = true;
       }
-      if (reset && (r = V.axpby(al, pa, zeros, py))) return r;
+    }
+    if (reset) {
+      if ((r = A.upload())) return r;
+      da::k_neg_grad<<<ew, 256, 0, st>>>(dv);
+      if ((r = check_launch(c))) return r;
     }
 
     // line search, all searching members together
@@ -240,98 +214,94 @@ extern "C" da_status da_assimilate(da_ctx* c, double* s, int max_iter, const da_
       ls[b].start(mb[b].f, gd[b], s0, o.c1, o.c2, 1e-10, 1e-20, 1e20, o.max_ls_evals);
       searching[b] = 1;
     }
-    std::vector<double> ft(B), dg;
     for (;;) {
       bool anys = false;
       for (int b = 0; b < B; ++b) anys |= searching[b] != 0;
       if (!anys) break;
       // xt = x + stp d for searching members, x otherwise
-      DA_TRY_CUDA(c, cudaMemcpyAsync(c->xt, c->x, B * len * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      std::vector<double> al(B, 0.0);
       for (int b = 0; b < B; ++b) {
-        al[b] = searching[b] ? ls[b].stp() : 0.0;
-        pa[b] = searching[b] ? V.member(c->d, b) : nullptr;
-        py[b] = searching[b] ? V.member(c->xt, b) : nullptr;
+        A.mask()[b] = searching[b];
+        A.stp()[b] = searching[b] ? ls[b].stp() : 0.0;
       }
-      if ((r = V.axpby(al, pa, ones, py))) return r;
-      if ((r = da_cost_grad(c, c->xt, ft.data(), c->gt, st))) return r;
-      for (int b = 0; b < B; ++b) {
-        pa[b] = searching[b] ? V.member(c->gt, b) : nullptr;
-        pb[b] = searching[b] ? V.member(c->d, b) : nullptr;
-      }
-      if ((r = V.dot(pa, pb, dg))) return r;
+      if ((r = A.upload())) return r;
+      da::k_trial<<<ew, 256, 0, st>>>(dv);
+      if ((r = check_launch(c))) return r;
+      if ((r = da_cost_grad(c, XT, c->lb_J, GT, st))) return r;
+      da::k_dot_gt_d<<<B, da::kBlasThreads, 0, st>>>(dv);
+      if ((r = check_launch(c))) return r;
+      if ((r = read_scalars(c, st))) return r;
+      bool accept_any = false;
+      for (int b = 0; b < B; ++b) A.mask()[b] = 0;
       for (int b = 0; b < B; ++b) {
         if (!searching[b]) continue;
-        if (!std::isfinite(ft[b]) || !std::isfinite(dg[b])) {
+        const double ft = hJ[b], dg = sc(b, da::SC_DG);
+        if (!std::isfinite(ft) || !std::isfinite(dg)) {
           searching[b] = 0;
           mb[b].state = 3;
           continue;
         }
-        const int act = ls[b].step(ft[b], dg[b]);
+        const int act = ls[b].step(ft, dg);
         if (act == da::MoreThuente::EVALUATE) continue;
         searching[b] = 0;
         const bool ok = act == da::MoreThuente::CONVERGED;
-        if (ok || ft[b] < mb[b].f) {
-          // accept: new pair in a free slot, s = xt - x, y = gt - g
+        if (ok || ft < mb[b].f) {
+          // accept: the new pair goes to a free slot, s = xt - x, y = gt - g
           int freeslot = 0;
           for (int t = 0; t < slots; ++t)
             if (std::find(mb[b].pairs.begin(), mb[b].pairs.end(), t) == mb[b].pairs.end()) {
               freeslot = t;
               break;
             }
-          double* Sd = Sslot(freeslot, b);
-          double* Yd = Yslot(freeslot, b);
-          DA_TRY_CUDA(c, cudaMemcpyAsync(Sd, V.member(c->xt, b), len * sizeof(double), cudaMemcpyDeviceToDevice, st));
-          DA_TRY_CUDA(c, cudaMemcpyAsync(Yd, V.member(c->gt, b), len * sizeof(double), cudaMemcpyDeviceToDevice, st));
-          std::vector<double> neg(B, 0.0);
-          std::vector<const double*> xs(B, nullptr);
-          std::vector<double*> ys(B, nullptr);
-          neg[b] = -1.0;
-          xs[b] = V.member(c->x, b);
-          ys[b] = Sd;
-          if ((r = V.axpby(neg, xs, ones, ys))) return r;
-          xs[b] = V.member(c->g, b);
-          ys[b] = Yd;
-          if ((r = V.axpby(neg, xs, ones, ys))) return r;
-          std::vector<const double*> sa(B, nullptr), ya(B, nullptr);
-          sa[b] = Sd;
-          ya[b] = Yd;
-          std::vector<double> sy, yy;
-          if ((r = V.dot(sa, ya, sy))) return r;
-          if ((r = V.dot(ya, ya, yy))) return r;
-          if (sy[b] > 1e-16 * yy[b]) {
-            if ((int)mb[b].pairs.size() == m) {
-              mb[b].pairs.erase(mb[b].pairs.begin());
-              mb[b].rho.erase(mb[b].rho.begin());
-            }
-            mb[b].pairs.push_back(freeslot);
-            mb[b].rho.push_back(1.0 / sy[b]);
-          }
-          DA_TRY_CUDA(c, cudaMemcpyAsync(V.member(c->x, b), V.member(c->xt, b), len * sizeof(double),
-                                         cudaMemcpyDeviceToDevice, st));
-          DA_TRY_CUDA(c, cudaMemcpyAsync(V.member(c->g, b), V.member(c->gt, b), len * sizeof(double),
-                                         cudaMemcpyDeviceToDevice, st));
-          mb[b].f = ft[b];
+          mb[b].pending = freeslot;
+          A.mask()[b] = 1;
+          A.aslot()[b] = freeslot;
+          accept_any = true;
+          mb[b].f = ft;
           mb[b].iters = it + 1;
-          J_hist[(size_t)b * (max_iter + 1) + it + 1] = ft[b];
+          J_hist[(size_t)b * (max_iter + 1) + it + 1] = ft;
         }
         if (!ok) mb[b].state = 2;
       }
+      if (accept_any) {
+        if ((r = A.upload())) return r;
+        da::k_accept<<<B, da::kBlasThreads, 0, st>>>(dv);
+        if ((r = check_launch(c))) return r;
+      }
     }
-    for (int b = 0; b < B; ++b) pa[b] = V.member(c->g, b);
-    if ((r = V.dot(pa, pa, tmp))) return r;
-    for (int b = 0; b < B; ++b) mb[b].gnorm = std::sqrt(tmp[b]);
+    // end of the iteration: pair tests and gradient norms
+    da::k_gnorm2<<<B, da::kBlasThreads, 0, st>>>(dv);
+    if ((r = check_launch(c))) return r;
+    if ((r = read_scalars(c, st))) return r;
+    for (int b = 0; b < B; ++b) {
+      if (mb[b].pending >= 0) {
+        const double sy = sc(b, da::SC_SY), yy = sc(b, da::SC_YY);
+        if (sy > 1e-16 * yy) {
+          if ((int)mb[b].pairs.size() == m) {
+            mb[b].pairs.erase(mb[b].pairs.begin());
+            mb[b].rho.erase(mb[b].rho.begin());
+          }
+          mb[b].pairs.push_back(mb[b].pending);
+          mb[b].rho.push_back(1.0 / sy);
+        }
+        mb[b].pending = -1;
+      }
+      mb[b].gnorm = std::sqrt(sc(b, da::SC_GG));
+    }
   }
   bool diverged = false, failed = false;
+  std::string who;
   for (int b = 0; b < B; ++b) {
     iters_done[b] = mb[b].iters;
     for (int it = mb[b].iters + 1; it <= max_iter; ++it) J_hist[(size_t)b * (max_iter + 1) + it] = mb[b].f;
-    diverged |= mb[b].state == 3;
-    failed |= mb[b].state == 2;
+    const da_status ms = mb[b].state == 3 ? DA_EDIVERGED : mb[b].state == 2 ? DA_ENOTCONV : DA_OK;
+    if (member_status) member_status[b] = ms;
+    diverged |= ms == DA_EDIVERGED;
+    failed |= ms == DA_ENOTCONV;
+    if (ms != DA_OK) who += (who.empty() ? "" : ", ") + std::to_string(b);
   }
-  DA_TRY_CUDA(c, cudaMemcpyAsync(s, c->x, B * len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  DA_TRY_CUDA(c, cudaMemcpyAsync(s, X, B * len * sizeof(double), cudaMemcpyDeviceToDevice, st));
   DA_TRY_CUDA(c, cudaStreamSynchronize(st));
-  if (diverged) return fail(c, DA_EDIVERGED, "non-finite cost or gradient");
-  if (failed) return fail(c, DA_ENOTCONV, "line search failed (step-size collapse)");
+  if (diverged) return fail(c, DA_EDIVERGED, "non-finite cost or gradient (members with a non-OK status: " + who + ")");
+  if (failed) return fail(c, DA_ENOTCONV, "line search failed, step-size collapse (members " + who + ")");
   return DA_OK;
 }

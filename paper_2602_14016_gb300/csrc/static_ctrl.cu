@@ -11,7 +11,6 @@
 
 #include <cmath>
 #include <mutex>
-#include <vector>
 
 #include "../../include/da.h"
 #include "kernels.cuh"
@@ -105,38 +104,63 @@ cudaError_t launch(const double* s, double* omega0, double2* rows, const double2
 }
 
 // Per-device set-up: device addresses of the two arrays and the twiddles.
+// The states live in a fixed array that never moves, and a caller gets a
+// copy taken under the lock, so concurrent first calls on different devices
+// cannot invalidate each other's view.
+constexpr int kMaxDevices = 64;
 struct DeviceState {
   bool ready = false;
   double2* rows = nullptr;
   double2* tw = nullptr;
 };
 static std::mutex g_mu;
-static std::vector<DeviceState> g_dev;
+static DeviceState g_dev[kMaxDevices];
 
-static cudaError_t setup_current_device(DeviceState** out) {
+static cudaError_t setup_current_device(DeviceState* out, const char** msg) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) {
+    *msg = "device ordinal beyond the 64 devices the static control map keeps state for";
+    return cudaErrorInvalidDevice;
+  }
   std::lock_guard<std::mutex> lock(g_mu);
-  if ((int)g_dev.size() <= dev) g_dev.resize(dev + 1);
   DeviceState& d = g_dev[dev];
   if (!d.ready) {
-    e = cudaGetSymbolAddress((void**)&d.rows, g_rows);
+    DeviceState t;
+    e = cudaGetSymbolAddress((void**)&t.rows, g_rows);
     if (e != cudaSuccess) return e;
-    e = cudaGetSymbolAddress((void**)&d.tw, g_tw);
+    e = cudaGetSymbolAddress((void**)&t.tw, g_tw);
     if (e != cudaSuccess) return e;
     double2 host[kMaxN];
     const long double pi = 3.141592653589793238462643383279502884L;
-    for (int t = 0; t < kMaxN; ++t) {
-      const long double a = -2.0L * pi * (long double)t / (long double)kMaxN;
-      host[t] = make_double2((double)cosl(a), (double)sinl(a));
+    for (int i = 0; i < kMaxN; ++i) {
+      const long double a = -2.0L * pi * (long double)i / (long double)kMaxN;
+      host[i] = make_double2((double)cosl(a), (double)sinl(a));
     }
     e = cudaMemcpyToSymbol(g_tw, host, sizeof(host));
     if (e != cudaSuccess) return e;
-    d.ready = true;
+    t.ready = true;
+    d = t;
   }
-  *out = &d;
+  *out = d;
   return cudaSuccess;
+}
+
+// W(k) of kinds 1..3 is monotone in |k|, so it is finite and non-negative on
+// the retained set (1 <= |k| <= sqrt(2) K) iff it is at both ends.
+static bool kernel_finite_on_retained_set(int kind, double param, double nu, int n) {
+  const double K = (double)((n - 1) / 3);
+  const double ks[2] = {1.0, std::sqrt(2.0) * K};
+  for (double k : ks) {
+    double W = 1.0;
+    if (kind == 1) W = std::exp(-param * k);
+    else if (kind == 2) W = std::pow(k, -2.0 * param);
+    else if (kind == 3) W = std::exp(-nu * param * k * k);
+    const double m = k * std::sqrt(W);
+    if (!std::isfinite(W) || !(W >= 0.0) || !std::isfinite(m)) return false;
+  }
+  return true;
 }
 
 }  // namespace st
@@ -159,16 +183,22 @@ extern "C" da_status da_omega_from_control_static(int n, double nu, const da_ker
     *msg = "kernel kind must be identity, exp_abs, frac or exp_sq (tables need device memory)";
     return DA_EINVAL;
   }
-  if (!std::isfinite(kernel->param) || !(nu >= 0.0)) {
+  if (!std::isfinite(kernel->param) || !(nu >= 0.0) || !std::isfinite(nu)) {
     *msg = "kernel parameter must be finite and nu >= 0";
     return DA_EINVAL;
   }
-  da::st::DeviceState* d = nullptr;
-  cudaError_t e = da::st::setup_current_device(&d);
+  if (!da::st::kernel_finite_on_retained_set(kernel->kind, kernel->param, nu, n)) {
+    *msg = "kernel W is not finite and non-negative on the retained set";
+    return DA_EINVAL;
+  }
+  da::st::DeviceState dst;
+  const char* setup_msg = nullptr;
+  cudaError_t e = da::st::setup_current_device(&dst, &setup_msg);
   if (e != cudaSuccess) {
-    *msg = cudaGetErrorString(e);
+    *msg = setup_msg ? setup_msg : cudaGetErrorString(e);
     return DA_ECUDA;
   }
+  const da::st::DeviceState* d = &dst;
   cudaStream_t st = (cudaStream_t)stream;
   const int kind = kernel->kind;
   const double a = kernel->param;

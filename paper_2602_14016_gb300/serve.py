@@ -49,7 +49,8 @@ class Job:
     t_done: float = float("nan")
     J_hist: Optional[np.ndarray] = None
     iters_done: int = 0
-    status: int = -1
+    status: int = -1  # DA_OK, DA_ENOTCONV (stopped on a line-search failure), or a failure status
+    error: str = ""
     s: Optional[np.ndarray] = None
 
     @property
@@ -76,7 +77,9 @@ def context_bytes(n: int, nsteps: int, px: int, every: int, ckpt_every: int, bat
         kk = min(ckpt_every, nsteps)
         b += batch * kk * 8 * n * n * 8 + ((nsteps + kk - 1) // kk) * comp
     slots = memory + 1
-    b += batch * (5 + 2 * slots) * n * n * 8 + batch * (((n * n + 8191) // 8192) + 3) * 8 + 2 * batch * 8
+    # optimiser: vector banks, device scalars and costs, argument tables
+    b += batch * (5 + 2 * slots) * n * n * 8 + batch * 7 * 8 + (3 * batch + batch * memory) * 4
+    b += (batch + batch * memory) * 8
     return int(b)
 
 
@@ -116,17 +119,23 @@ class CudaExecutor:
         cfg = api.Config(n=job.n, nsteps=job.nsteps, dt=job.dt, nu=job.nu, forcing=job.forcing, nf=job.nf,
                          px=job.px, every=job.every, kernels=[api.KernelSpec(*job.kernel)],
                          ckpt_every=job.ckpt_every)
+        from . import _native
+
         with torch.cuda.device(self.device), torch.cuda.stream(st):
-            ctx = api.Context(cfg, self.device)
+            ctx = None
             try:
+                ctx = api.Context(cfg, self.device)
                 ctx.set_observations(torch.from_numpy(job.m).to(ctx.device), stream=st)
                 s = torch.from_numpy(job.s0).to(ctx.device).contiguous()
-                J, it, status = ctx.assimilate(s, job.iters, stream=st)
+                res = ctx.assimilate(s, job.iters, stream=st)
                 st.synchronize()
-                job.J_hist, job.iters_done, job.status = J[0], int(it[0]), int(status)
+                job.J_hist, job.iters_done, job.status = res.J_hist[0], int(res.iters[0]), int(res.member_status[0])
                 job.s = s.cpu().numpy()
+            except _native.DAError as e:  # a failed job is recorded, not lost with its worker thread
+                job.status, job.error = e.status, str(e)
             finally:
-                ctx.close()
+                if ctx is not None:
+                    ctx.close()
 
 
 class FakeExecutor:
@@ -219,7 +228,11 @@ class Server:
             th.join()
         makespan = max(j.t_done for j in jobs) - min(j.arrival for j in jobs)
         lat = np.array([j.latency for j in jobs])
-        return {"jobs": len(jobs), "solves_per_s": len(jobs) / makespan, "makespan_s": makespan,
+        # a solve returns a control: converged, out of iterations, or stopped by
+        # the line search (DA_ENOTCONV); anything else is a failed job
+        solved = [j for j in jobs if j.status in (0, 6)]
+        return {"jobs": len(jobs), "solves": len(solved), "failed": len(jobs) - len(solved),
+                "solves_per_s": len(solved) / makespan, "makespan_s": makespan,
                 "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                 "peak_bytes": self.peak_bytes, "peak_running": self.peak_running}
 

@@ -14,7 +14,7 @@ def declared_functions():
     with open(os.path.join(ROOT, "include", "da.h")) as f:
         src = f.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(da_[a-z_]+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(da_[a-z0-9_]+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
@@ -93,3 +93,22 @@ def test_plan_variant_queries_on_the_host(lib):
     chosen = ctypes.c_int(-7)
     assert lib.da_autotune(None, 4, ctypes.byref(chosen), None) == 1
     assert chosen.value == -7
+
+
+@pytest.mark.parametrize("n,kind,param,frag", [
+    (512, 0, 0.0, b"256"),
+    (64, 4, 0.0, b"table"),
+    (64, 1, -800.0, b"finite"),   # exp(800 |k|) overflows on the retained set
+    (256, 2, -400.0, b"finite"),  # |k|^800 overflows at |k| = sqrt(2) 85
+    (64, 1, float("inf"), b"finite"),
+])
+def test_static_control_map_rejects_on_the_host(lib, n, kind, param, frag):
+    """da_omega_from_control_static validates sizes and kernels before any
+    device work, so it answers DA_EINVAL here without a GPU."""
+    from paper_2602_14016_gb300 import _native as N
+
+    k = N.Kernel(kind, param, None)
+    msg = ctypes.c_char_p()
+    dummy = ctypes.c_void_p(16)
+    st = lib.da_omega_from_control_static(n, 1e-2, ctypes.byref(k), dummy, dummy, None, ctypes.byref(msg))
+    assert st == N.DA_EINVAL and frag in msg.value, msg.value

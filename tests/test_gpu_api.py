@@ -89,6 +89,29 @@ def test_graph_replay_equals_direct_launches(api, ckpt):
         J2, g2 = graph.cost_grad(s * scale)
         assert torch.equal(J1, J2) and torch.equal(g1, g2)
     s1, s2 = (s * 0.9).contiguous(), (s * 0.9).contiguous()
-    H1, i1, _ = direct.assimilate(s1, 3)
-    H2, i2, _ = graph.assimilate(s2, 3)
+    H1, i1, _, _ = direct.assimilate(s1, 3)
+    H2, i2, _, _ = graph.assimilate(s2, 3)
     assert np.array_equal(H1, H2) and np.array_equal(i1, i2) and torch.equal(s1, s2)
+
+
+def test_trajectory_larger_than_device_memory_gives_enomem(api):
+    """A window whose stage-field store (64 n^2 bytes per step) is twice the
+    device's memory: da_create returns DA_ENOMEM with a message, frees what it
+    had allocated, and the process carries on."""
+    from paper_2602_14016_gb300._native import DAError, DA_ENOMEM
+
+    free0, total = torch.cuda.mem_get_info()
+    n = 1024
+    nsteps = int(2 * total // (64 * n * n)) // 10 * 10
+    cfg = api.Config(n=n, nsteps=nsteps, dt=1e-4, nu=1e-3, px=32, every=nsteps,
+                     kernels=[api.KernelSpec("exp_abs", 0.5)])
+    with pytest.raises(DAError) as e:
+        api.Context(cfg)
+    assert e.value.status == DA_ENOMEM and "cudaMalloc" in str(e.value)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (64 << 20)  # nothing of the failed context stays allocated
+    ctx = api.Context(small(api))
+    ctx.set_observations(torch.zeros((1, ctx.nt, 64, 2), dtype=torch.float64, device="cuda"))
+    J, g = ctx.cost_grad(torch.from_numpy(synthetic.random_field(32, 3)[None]).cuda())
+    assert torch.isfinite(J).all() and torch.isfinite(g).all()

@@ -75,3 +75,40 @@ def test_static_control_map_rejects_sizes_beyond_its_scratch(lib):
     dummy = ctypes.c_void_p(1)
     st = lib.da_omega_from_control_static(512, 1e-2, ctypes.byref(k), dummy, dummy, None, ctypes.byref(msg))
     assert st == N.DA_EINVAL and b"256" in msg.value
+
+
+def test_static_control_map_from_two_threads(lib):
+    """Two host threads, each on its own stream, take turns (calls that
+    overlap on the GPU would race on the shared scratch); every result
+    matches the context entry point."""
+    import threading
+
+    from paper_2602_14016_gb300 import api
+
+    n, nu, kind, param = 64, 1e-2, "exp_abs", 0.5
+    lock = threading.Lock()
+    fields = {i: torch.from_numpy(synthetic.random_field(n, 200 + i)).cuda() for i in range(2)}
+    out = {}
+
+    def work(i):
+        st = torch.cuda.Stream()
+        for rep in range(3):
+            with lock:
+                with torch.cuda.stream(st):
+                    r = static_map(lib, n, nu, kind, param, fields[i])
+                st.synchronize()
+            out[(i, rep)] = r
+
+    th = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    ctx = api.Context(api.Config(n=n, nsteps=1, dt=1e-3, nu=nu, px=8, every=1,
+                                 kernels=[api.KernelSpec(kind, param)], store=False))
+    for i in range(2):
+        ref = ctx.omega_from_control(fields[i][None])[0]
+        torch.cuda.synchronize()
+        for rep in range(3):
+            assert rel(out[(i, rep)], ref) < TOL
+    ctx.close()
