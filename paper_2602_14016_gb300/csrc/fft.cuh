@@ -152,9 +152,17 @@ template <> struct Plan<16, 0> { using two = Radices<4, 4>; using one = Radices<
 template <> struct Plan<32, 0> { using two = Radices<4, 8>; using one = Radices<4, 8>; static constexpr int threads = 32; };
 template <> struct Plan<64, 0> { using two = Radices<4, 4, 4>; using one = Radices<4, 4, 4>; static constexpr int threads = 32; };
 template <> struct Plan<64, 1> { using two = Radices<8, 8>; using one = Radices<8, 8>; static constexpr int threads = 32; };
+// Radix-2 plans: 1.2x the FP64 instructions of the radix-4 ones, but each
+// thread's chain is about half as long (34 instead of 60 instructions per
+// 64-point transform).  On GB300 a lone warp issues one FP64 instruction per
+// ~67 SM clocks whatever its active lanes, so the small grids at small
+// batches, whose pass kernels are bound by that chain, run faster on them.
+template <> struct Plan<32, 1> { using two = Radices<2, 2, 2, 2, 2>; using one = Radices<2, 2, 2, 2, 2>; static constexpr int threads = 32; };
+template <> struct Plan<64, 2> { using two = Radices<2, 2, 2, 2, 2, 2>; using one = Radices<2, 2, 2, 2, 2, 2>; static constexpr int threads = 64; };
 template <> struct Plan<128, 0> { using two = Radices<4, 4, 8>; using one = Radices<4, 4, 8>; static constexpr int threads = 64; };
 template <> struct Plan<128, 1> { using two = Radices<8, 4, 4>; using one = Radices<8, 4, 4>; static constexpr int threads = 64; };
 template <> struct Plan<128, 2> { using two = Radices<4, 4, 8>; using one = Radices<4, 4, 8>; static constexpr int threads = 32; };
+template <> struct Plan<128, 3> { using two = Radices<2, 2, 2, 2, 2, 2, 2>; using one = Radices<2, 2, 2, 2, 2, 2, 2>; static constexpr int threads = 128; };
 template <> struct Plan<256, 0> { using two = Radices<4, 4, 4, 4>; using one = Radices<4, 4, 4, 4>; static constexpr int threads = 128; };
 template <> struct Plan<256, 1> { using two = Radices<8, 8, 4>; using one = Radices<8, 8, 4>; static constexpr int threads = 64; };
 template <> struct Plan<256, 2> { using two = Radices<4, 4, 4, 4>; using one = Radices<4, 4, 4, 4>; static constexpr int threads = 64; };
@@ -167,7 +175,7 @@ template <> struct Plan<1024, 2> { using two = Radices<8, 8, 4, 4>; using one = 
 
 // Number of plan variants of each size (the instantiations in inst_n*.cu).
 constexpr int plan_count(int n) {
-  return n == 64 ? 2 : (n == 128 || n == 256 || n == 512 || n == 1024) ? 3 : 1;
+  return n == 32 ? 2 : n == 64 ? 3 : n == 128 ? 4 : (n == 256 || n == 512 || n == 1024) ? 3 : 1;
 }
 
 template <int N, int V = 0>
@@ -249,11 +257,13 @@ __device__ __forceinline__ void run_stages(double2* buf, const double2* tw, Radi
 //
 // Per stage with L > 1 the table holds, slot-major (slot j of butterfly
 // class k at j * L + k):
+//   R = 2: t1, c1;
 //   R = 4: t1 t2 t3 (for S = -1), c1, c2, r31;
 //   R = 8: t1..t7, c1, c2, c4, r62 = c6/c2, r51 = c5/c1, r73 = c7/c3,
 //          r31 = c3/c1, q = cos(pi/4) c1.
 
 template <int R> struct FoldSlots { static constexpr int value = 0; };  // untwiddled first stages only
+template <> struct FoldSlots<2> { static constexpr int value = 2; };
 template <> struct FoldSlots<4> { static constexpr int value = 6; };
 template <> struct FoldSlots<8> { static constexpr int value = 15; };
 
@@ -280,6 +290,15 @@ __device__ __forceinline__ double2 tan_rot(double2 a, double t) {
 __device__ __forceinline__ void fma_pair(double2 e, double2 z, double c, double2& plus, double2& minus) {
   plus = make_double2(fma(c, z.x, e.x), fma(c, z.y, e.y));
   minus = make_double2(fma(-c, z.x, e.x), fma(-c, z.y, e.y));
+}
+
+// Twiddled radix-2 butterfly with a folded twiddle: a0 +- c1 z1, six FP64
+// instructions.
+template <int S>
+__device__ __forceinline__ void dft2_folded(double2* a, const double* T, int k, int L) {
+  const double sg = S < 0 ? 1.0 : -1.0;
+  const double2 z1 = tan_rot(a[1], sg * T[k]);
+  fma_pair(a[0], z1, T[L + k], a[0], a[1]);
 }
 
 // Twiddled radix-4 butterfly with folded twiddles (table T, class k, L).
@@ -348,7 +367,8 @@ __device__ __forceinline__ void stockham_stage_folded(double2* buf, const double
       if constexpr (L == 1) {
         dftR<R, S>(a[jb]);
       } else {
-        static_assert(R == 4 || R == 8, "folded twiddles for radix 4 and 8");
+        static_assert(R == 2 || R == 4 || R == 8, "folded twiddles for radix 2, 4 and 8");
+        if constexpr (R == 2) dft2_folded<S>(a[jb], T, k, L);
         if constexpr (R == 4) dft4_folded<S>(a[jb], T, k, L);
         if constexpr (R == 8) dft8_folded<S>(a[jb], T, k, L);
       }
@@ -402,7 +422,10 @@ inline void fold_fill(double* out, int n, Radices<R, Rs...>) {
         c[m] = std::cos(th);
         t[m] = std::tan(th);
       }
-      if (R == 4) {
+      if (R == 2) {
+        out[k] = t[1];
+        out[L + k] = c[1];
+      } else if (R == 4) {
         const double v[6] = {t[1], t[2], t[3], c[1], c[2], c[3] / c[1]};
         for (int j = 0; j < 6; ++j) out[j * L + k] = v[j];
       } else {

@@ -31,3 +31,19 @@ def noisy_observations(obs: np.ndarray, seed: int, level: float = 0.01) -> np.nd
     """obs + level * RMS(obs) * N(0, 1) draws (1 % noise reading)."""
     rms = float(np.sqrt(np.mean(obs**2)))
     return obs + level * rms * synthetic.gaussian_draws(obs.shape, seed)
+
+
+def kolmogorov256_oracle_member(args):
+    """Oracle cost, gradient and compact lambda_0 of one member of the 256^2
+    Kolmogorov window (spawned worker: imports only the oracle and numpy)."""
+    import oracle
+
+    nsteps, kernel, kp, m, seed_guess = args
+    n = 256
+    P = oracle.Problem(n=n, nsteps=nsteps, dt=2e-3, nu=1e-2, forcing="kolmogorov", amp=1.0, nf=4, px=16, every=20,
+                       kernel=kernel, kparam=kp)
+    s = oracle.control_from_omega(P, synthetic.random_vorticity_hat(n, seed_guess))
+    J, g, lam0 = oracle.cost_grad(P, s, m)
+    K = (n - 1) // 3
+    rows = list(range(0, K + 1)) + list(range(n - K, n))
+    return J, g, lam0[rows, : K + 1]

@@ -26,7 +26,8 @@ def cu(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-VARIANTS = [(n, v) for n in (16, 32, 64, 128, 256, 512, 1024) for v in range({64: 2}.get(n, 3 if n >= 128 else 1))]
+PLAN_COUNTS = {16: 1, 32: 2, 64: 3, 128: 4, 256: 3, 512: 3, 1024: 3}
+VARIANTS = [(n, v) for n in PLAN_COUNTS for v in range(PLAN_COUNTS[n])]
 
 
 def test_plan_counts_match_the_library(api):
@@ -64,7 +65,7 @@ def test_set_plan_rejects_out_of_range(api):
     cfg = api.Config(n=64, nsteps=4, dt=1e-2, nu=1e-2, px=8, every=4)
     ctx = api.Context(cfg)
     with pytest.raises(Exception):
-        ctx.set_plan(2)
+        ctx.set_plan(PLAN_COUNTS[64])
     with pytest.raises(Exception):
         ctx.set_plan(-1)
 
@@ -83,7 +84,7 @@ def test_autotune_keeps_the_fastest_and_later_contexts_reuse_it(api):
     s = control(80)
     J0, g0 = ctx.cost_grad(s)  # still in flight when the tuner starts: it must wait for it
     chosen, ms = ctx.autotune(steps=4)
-    assert len(ms) == 3 and all(t > 0 for t in ms)
+    assert len(ms) == PLAN_COUNTS[128] and all(t > 0 for t in ms)
     assert chosen == int(np.argmin(ms)) and ctx.plan == chosen
     # observations survive the tuning; the evaluation is the same up to rounding
     J1, g1 = ctx.cost_grad(s)
