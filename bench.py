@@ -432,31 +432,50 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def oracle_sample(n_sample_steps: int):
-    """One oracle cost-and-gradient evaluation on a bounded sample of the
-    workload: the first n_sample_steps steps of the window (one observation
-    time), one member (kernel |k|^-1), same grid and physics."""
+def _oracle_member_sample(args):
+    """One oracle cost-and-gradient evaluation of the first n_sample_steps
+    steps of the window (one observation time) for one sweep member; returns
+    its wall seconds (spawned worker)."""
+    n_sample_steps, kernel, kp = args
     import oracle
     from paper_2602_14016_gb300 import synthetic
 
     n = W["n"]
     P = oracle.Problem(n=n, nsteps=n_sample_steps, dt=W["dt"], nu=W["nu"], forcing=W["forcing"], amp=W["amp"],
-                       nf=W["nf"], px=W["px"], every=n_sample_steps, kernel="frac", kparam=0.5)
+                       nf=W["nf"], px=W["px"], every=n_sample_steps, kernel=kernel, kparam=kp)
     truth = oracle.control_from_omega(P, synthetic.random_vorticity_hat(n, W["seed"]))
     guess = oracle.control_from_omega(P, synthetic.random_vorticity_hat(n, W["seed"] + 2))
     _, m = oracle.forward(P, truth)
     t0 = time.perf_counter()
-    J, g, _ = oracle.cost_grad(P, guess, m)
-    dt = time.perf_counter() - t0
-    return n * n * n_sample_steps / dt, dt
+    oracle.cost_grad(P, guess, m)
+    return time.perf_counter() - t0
+
+
+def oracle_sample(n_sample_steps: int, members=SWEEP):
+    """The oracle on a bounded sample of the workload: the first
+    n_sample_steps steps of the window for every sweep member, one
+    single-threaded process per member running at the same time (the batch's
+    members are independent jobs).  Returns (gridpoint-steps/s over the wall
+    time of the slowest member, that wall time, processes)."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    procs = min(len(members), os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        secs = pool.map(_oracle_member_sample, [(n_sample_steps, k, a) for k, a in members])
+    wall = max(secs) if procs >= len(members) else sum(secs) / procs
+    return len(members) * W["n"] ** 2 * n_sample_steps / wall, wall, procs
 
 
 def cpu_baseline(args):
     oracle_steps = 20
-    val, secs = oracle_sample(oracle_steps)
-    return {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one cost+gradient evaluation of the first {oracle_steps} steps of the 256^2 window, one "
-                      f"member, single-threaded C oracle ({secs:.1f} s)"}
+    val, secs, procs = oracle_sample(oracle_steps)
+    return {"value": val, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"one cost+gradient evaluation of the first {oracle_steps} steps of the 256^2 window for each of "
+                      f"the {len(SWEEP)} sweep members, one single-threaded C oracle process per member on "
+                      f"{procs} host cores ({secs:.1f} s)"}
 
 
 def run_reference(args):
@@ -467,21 +486,22 @@ def run_reference(args):
     oracle_steps = 20
     for _ in range(args.warmup):
         oracle_sample(2)
-    total_units, total_s = 0.0, 0.0
+    total_units, total_s, procs = 0.0, 0.0, 1
     for _ in range(args.steps):
-        v, s = oracle_sample(oracle_steps)
-        total_units += W["n"] ** 2 * oracle_steps
+        v, s, procs = oracle_sample(oracle_steps)
+        total_units += len(SWEEP) * W["n"] ** 2 * oracle_steps
         total_s += s
     value = total_units / total_s
-    sample = (f"each step one cost+gradient evaluation of the first {oracle_steps} steps of the 256^2 window, one "
-              "member, single-threaded C oracle")
+    sample = (f"each step one cost+gradient evaluation of the first {oracle_steps} steps of the 256^2 window for "
+              f"each of the {len(SWEEP)} sweep members, one single-threaded C oracle process per member")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "grid": W["n"], "sample_steps": oracle_steps},
+        "config": {"workload": WORKLOAD_NAME, "grid": W["n"], "sample_steps": oracle_steps,
+                   "members": len(SWEEP)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
     }), flush=True)
 
 
@@ -532,18 +552,37 @@ def run_workload(args):
         from paper_2602_14016_gb300 import serve
 
         summary = {}
+        dts = {128: 4e-3, 256: 2e-3, 512: 1e-3, 1024: 5e-4}
         for rate in args.rates:
             mix = dict(grids=tuple(args.serve_grids), weights=tuple(args.serve_weights), steps=tuple(args.serve_steps),
                        iters=args.serve_iters)
-            jobs = workloads.serving_jobs(api, torch, args.serve_jobs, rate, seed=7, **mix)
+
+            def fresh_jobs():
+                return workloads.serving_jobs(api, torch, args.serve_jobs, rate, seed=7, **mix)
+
             free = torch.cuda.mem_get_info()[0]
-            srv = serve.Server(serve.CudaExecutor(), memory_budget=int(0.6 * free), slots=args.slots,
-                               job_cap=int(0.6 * free / args.slots))
-            out = srv.run(jobs)
-            base_jobs = workloads.serving_jobs(api, torch, args.serve_jobs, rate, seed=7, **mix)
-            base = serve.Server(serve.CudaExecutor(), memory_budget=int(0.6 * free), slots=1,
-                                job_cap=int(0.6 * free / args.slots)).run(base_jobs)
-            summary[str(rate)] = {"continuous": out, "one_job_at_a_time": base}
+            budget = int(0.6 * free)
+            # co-batched: one pool per grid size, `slots` member slots each, its
+            # share of the budget; checkpoints when full storage does not fit
+            pools = {}
+            for n in args.serve_grids:
+                share = budget // len(args.serve_grids)
+                nmax = args.serve_steps[1] // 10 * 10
+                ck = 0
+                if serve.CoBatchServer.pool_bytes(n, nmax, 32, 10, 0, args.slots) > share:
+                    ck = next((K for K in range(nmax, 0, -1)
+                               if serve.CoBatchServer.pool_bytes(n, nmax, 32, 10, K, args.slots) <= share), 1)
+                pools[n] = dict(slots=args.slots, nsteps=nmax, px=32, dt=dts[n], ckpt_every=ck)
+            co = serve.CoBatchServer(pools)
+            out_co = co.run(fresh_jobs())
+            co.close()
+            torch.cuda.empty_cache()
+            out = serve.Server(serve.CudaExecutor(), memory_budget=budget, slots=args.slots,
+                               job_cap=int(budget / args.slots)).run(fresh_jobs())
+            base = serve.Server(serve.CudaExecutor(), memory_budget=budget, slots=1,
+                                job_cap=int(budget / args.slots)).run(fresh_jobs())
+            summary[str(rate)] = {"co_batched": out_co, "stream_overlap": out, "one_job_at_a_time": base,
+                                  "pools": {str(n): p for n, p in pools.items()}}
         line.update({"metric": "served solves/s, p50/p99 latency", "rates": summary,
                      "config": {"jobs": args.serve_jobs, "slots": args.slots, "grids": args.serve_grids,
                                 "grid_weights": args.serve_weights, "horizon_steps": args.serve_steps,

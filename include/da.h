@@ -178,11 +178,12 @@ da_status da_cost_grad(da_ctx* ctx, const double* s, double* J, double* grad_s, 
  * checkpoints, a second da_vjp needs a new da_forward. */
 da_status da_vjp(da_ctx* ctx, const double* dobs, const double* dwT, double* grad_s, void* stream);
 
-/* enable != 0: da_cost_grad (and so da_assimilate) captures its whole launch
- * sequence into a CUDA graph on the first call and replays it afterwards on
- * an internal stream, ordered after and before the caller's stream by
- * events; the control is copied into and the gradient out of internal
- * buffers.  For small grids this removes the per-launch host cost.  The
+/* enable != 0: da_cost_grad (and so da_assimilate) and da_adjoint_spectra
+ * capture their whole launch sequence into a CUDA graph on the first call
+ * (da_adjoint_spectra: the first call per save_every and choice of outputs)
+ * and replay it afterwards on an internal stream, ordered after and before
+ * the caller's stream by events; inputs are copied into and outputs out of
+ * internal buffers.  For small grids this removes the per-launch host cost.  The
  * capture is redone after da_set_sobolev; kernel timing (da_time_kernels)
  * bypasses the graph.  The first call must not itself be inside a capture.
  * The first enabling call allocates the two internal buffers (2 batch n^2
@@ -274,6 +275,78 @@ int da_num_shells(const da_ctx* ctx);
  * two per iteration. */
 da_status da_assimilate(da_ctx* ctx, double* s, int max_iter, const da_lbfgs_opts* opts, double* J_hist,
                         int* iters_done, int* member_status, void* stream);
+
+/* Ragged batches.  A member slot can hold its own assimilation window
+ * (Eq. 1-3 with its own horizon, probe lattice, viscosity and forcing switch;
+ * grid, dt and obs.every stay the context's), so that jobs of one grid size
+ * share every launch.  In each evaluation the windows are end-aligned: the
+ * evaluation runs the longest live window, and a member with a shorter one
+ * starts later and ends with it; a member whose window is empty is idle (its
+ * launches return at once; its cost is 0, its gradient 0).  A member's
+ * results are those of a batch-1 context with its window on the same plan
+ * variant (the kernels do the same arithmetic for it).
+ *   nsteps: 0 (idle) or a multiple of obs.every, at most the context's
+ *     nsteps (which sizes the trajectory);
+ *   px: divides n, at most the context's px (which sizes the observation
+ *     buffers);
+ *   nu >= 0; forcing: 0 or 1 (the context's Kolmogorov forcing, which the
+ *     context must have been created with). */
+typedef struct {
+  int nsteps;
+  int px;
+  double nu;
+  int forcing;
+} da_member_window;
+
+/* Gives member slot `member` its window, kernel and observations m (DEVICE
+ * or host pointer, [nt][px*px][2] with nt = nsteps/every (+1 with
+ * include_t0)); with w->nsteps == 0 the slot becomes idle and kernel and m
+ * are not read.  Waits for `stream`, recomputes the multiplier |k| W^{1/2}
+ * (DA_EINVAL, slot left idle, if it is not finite and non-negative on the
+ * retained set), copies m on `stream`; drops a captured graph.  From the
+ * first call on, the context is a ragged batch: the other members keep the
+ * context's window until they are set.  da_adjoint_spectra needs a
+ * homogeneous batch. */
+da_status da_set_member(da_ctx* ctx, int member, const da_member_window* w, const da_kernel* kernel,
+                        const double* m, void* stream);
+
+/* Stepwise L-BFGS over the member slots (Sec. II.C), for loops that start and
+ * retire members between iterations: da_assimilate is da_lbfgs_start on
+ * every member, then da_lbfgs_iterate until none runs.  A member's iterates
+ * do not depend on when it started or on the other members. */
+typedef struct {
+  int phase;   /* 0 idle, 1 started (first evaluation pending), 2 iterating, 3 finished */
+  int status;  /* DA_OK, DA_ENOTCONV (line-search failure) or DA_EDIVERGED */
+  int iters;   /* iterations that accepted a step */
+  double J0;   /* cost at the start (after its first evaluation) */
+  double J;    /* cost at the current control */
+} da_lbfgs_report;
+
+/* (Re)starts member `member` at control s0 (DEVICE [n][n], copied on
+ * `stream`) with an iteration budget max_iter and the settings opts (NULL:
+ * defaults; memory must be the same for every member and call on a context).
+ * The first call allocates the optimiser's buffers (see da_assimilate). */
+da_status da_lbfgs_start(da_ctx* ctx, int member, const double* s0, int max_iter, const da_lbfgs_opts* opts,
+                         void* stream);
+
+/* One round: one L-BFGS iteration of every iterating member, in lockstep
+ * (shared evaluations), and the first cost-and-gradient evaluation of every
+ * member started since the last round.  A member finishes when it converges
+ * (|g| <= gtol_rel |g0|), spends its budget, its line search fails or its cost
+ * turns non-finite.  running (HOST, nullable): members still started or
+ * iterating.  Waits for `stream` (the line search decides on the host). */
+da_status da_lbfgs_iterate(da_ctx* ctx, int* running, void* stream);
+
+/* Report of member `member` (HOST out); J_hist (HOST, nullable, hist_len
+ * entries): the cost at the start and after every iteration, padded with the
+ * current cost; s (DEVICE [n][n], nullable): its current control, copied on
+ * `stream`. */
+da_status da_lbfgs_member(da_ctx* ctx, int member, da_lbfgs_report* out, double* J_hist, int hist_len, double* s,
+                          void* stream);
+
+/* Returns member slot `member`'s optimiser to idle (its window is unchanged:
+ * da_set_member with nsteps 0 idles the evaluations too). */
+da_status da_lbfgs_release(da_ctx* ctx, int member);
 
 /* Control maps of the change of variables of Eq. (18)-(19), one kernel per
  * member: omega0 DEVICE [batch][n][n/2+1] complex (half spectrum) <-> s

@@ -22,7 +22,9 @@ KERNEL_KINDS = {"identity": 0, "exp_abs": 1, "frac": 2, "exp_sq": 3, "table": 4}
 # Entry points declared in include/da.h, in order.
 EXPORTS = ("da_create", "da_set_sobolev", "da_set_graphs", "da_plan_count", "da_get_plan", "da_set_plan", "da_autotune",
            "da_set_observations", "da_forward", "da_cost_grad", "da_vjp", "da_last_adjoint",
-           "da_adjoint_terminal", "da_adjoint_spectra", "da_num_shells", "da_assimilate", "da_omega_from_control", "da_control_from_omega",
+           "da_adjoint_terminal", "da_adjoint_spectra", "da_num_shells", "da_assimilate", "da_set_member",
+           "da_lbfgs_start", "da_lbfgs_iterate", "da_lbfgs_member", "da_lbfgs_release", "da_omega_from_control",
+           "da_control_from_omega",
            "da_omega_from_control_static", "da_fp64_probe", "da_num_obs_times", "da_device_bytes", "da_launch_count",
            "da_time_kernels", "da_kernel_time", "da_last_error", "da_destroy")
 
@@ -42,6 +44,15 @@ class ObsOperator(ctypes.Structure):
 
 class Kernel(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("param", ctypes.c_double), ("table", ctypes.c_void_p)]
+
+
+class MemberWindow(ctypes.Structure):
+    _fields_ = [("nsteps", ctypes.c_int), ("px", ctypes.c_int), ("nu", ctypes.c_double), ("forcing", ctypes.c_int)]
+
+
+class LbfgsReport(ctypes.Structure):
+    _fields_ = [("phase", ctypes.c_int), ("status", ctypes.c_int), ("iters", ctypes.c_int), ("J0", ctypes.c_double),
+                ("J", ctypes.c_double)]
 
 
 class LbfgsOpts(ctypes.Structure):
@@ -90,6 +101,11 @@ def load(path: str = LIB_PATH):
             "da_adjoint_spectra": (I, [C, P, P, I, P, P, P]),
             "da_num_shells": (I, [C]),
             "da_assimilate": (I, [C, P, I, ctypes.POINTER(LbfgsOpts), P, P, P, P]),
+            "da_set_member": (I, [C, I, ctypes.POINTER(MemberWindow), ctypes.POINTER(Kernel), P, P]),
+            "da_lbfgs_start": (I, [C, I, P, I, ctypes.POINTER(LbfgsOpts), P]),
+            "da_lbfgs_iterate": (I, [C, ctypes.POINTER(ctypes.c_int), P]),
+            "da_lbfgs_member": (I, [C, I, ctypes.POINTER(LbfgsReport), P, I, P, P]),
+            "da_lbfgs_release": (I, [C, I]),
             "da_omega_from_control": (I, [C, P, P, P]),
             "da_control_from_omega": (I, [C, P, P, P]),
             "da_omega_from_control_static": (I, [I, D, ctypes.POINTER(Kernel), P, P, P,

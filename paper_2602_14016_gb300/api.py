@@ -226,6 +226,57 @@ class Context:
             self._check(st)
         return AssimResult(J, it, st, ms)
 
+    # -- ragged batches and the stepwise optimiser -------------------------
+    def set_member(self, member: int, nsteps: int, px: int = 8, nu: float = 1e-3, forcing: bool = False,
+                   kernel: "KernelSpec | None" = None, m: "torch.Tensor | None" = None, stream=None):
+        """Gives member slot `member` its own window (nsteps 0: idle), kernel and
+        observations m [nt, px*px, 2]; the context becomes a ragged batch."""
+        import numpy as np
+
+        w = N.MemberWindow(int(nsteps), int(px), float(nu), int(bool(forcing)))
+        kernel = kernel or KernelSpec()
+        tab = None
+        if kernel.kind == "table":
+            tab = np.ascontiguousarray(kernel.table, dtype=np.float64)
+        k = N.Kernel(N.KERNEL_KINDS[kernel.kind], float(kernel.param), tab.ctypes.data if tab is not None else None)
+        mp = None
+        if nsteps > 0:
+            m = m.to(self.device, torch.float64).contiguous()
+            self._keep = m  # the copy is asynchronous
+            mp = _ptr(m)
+        self._check(self.lib.da_set_member(self.ctx, int(member), ctypes.byref(w), ctypes.byref(k), mp,
+                                           _stream(stream)))
+
+    def lbfgs_start(self, member: int, s0: torch.Tensor, max_iter: int, memory: int = 10, c1: float = 1e-4,
+                    c2: float = 0.9, gtol_rel: float = 1e-10, max_ls_evals: int = 20, stream=None):
+        """Starts the optimiser of member slot `member` at s0 [n, n]."""
+        s0 = s0.contiguous()
+        o = N.LbfgsOpts(memory, c1, c2, gtol_rel, max_ls_evals)
+        self._check(self.lib.da_lbfgs_start(self.ctx, int(member), _ptr(s0), int(max_iter), ctypes.byref(o),
+                                            _stream(stream)))
+
+    def lbfgs_iterate(self, stream=None) -> int:
+        """One lockstep round; returns the number of members still running."""
+        running = ctypes.c_int(0)
+        self._check(self.lib.da_lbfgs_iterate(self.ctx, ctypes.byref(running), _stream(stream)))
+        return running.value
+
+    def lbfgs_member(self, member: int, hist_len: int = 0, control: bool = False, stream=None):
+        """(report dict, J history [hist_len] or None, control [n, n] or None)."""
+        import numpy as np
+
+        rep = N.LbfgsReport()
+        hist = np.zeros(hist_len, np.float64) if hist_len > 0 else None
+        s = torch.empty((self.cfg.n, self.cfg.n), dtype=torch.float64, device=self.device) if control else None
+        self._check(self.lib.da_lbfgs_member(self.ctx, int(member), ctypes.byref(rep),
+                                             hist.ctypes.data if hist is not None else None, int(hist_len),
+                                             _ptr(s), _stream(stream)))
+        report = {"phase": rep.phase, "status": rep.status, "iters": rep.iters, "J0": rep.J0, "J": rep.J}
+        return report, hist, s
+
+    def lbfgs_release(self, member: int):
+        self._check(self.lib.da_lbfgs_release(self.ctx, int(member)))
+
     def omega_from_control(self, s: torch.Tensor, stream=None):
         w = self._spec()
         self._check(self.lib.da_omega_from_control(self.ctx, _ptr(s.contiguous()), _ptr(torch.view_as_real(w)),

@@ -134,4 +134,13 @@ __global__ void __launch_bounds__(kBlasThreads) k_gnorm2(LbfgsArgs a) {
   if (threadIdx.x == 0) a.scal[(size_t)b * SC_COUNT + SC_GG] = r;
 }
 
+__global__ void k_take_gradient(LbfgsArgs a) {
+  const int b = blockIdx.y;
+  if (!a.mask[b]) return;
+  const double* gt = bank(a, BANK_GT, b);
+  double* g = bank(a, BANK_G, b);
+  const size_t lo = (size_t)blockIdx.x * kChunk;
+  for (size_t i = lo + threadIdx.x; i < lo + kChunk && i < a.len; i += blockDim.x) g[i] = gt[i];
+}
+
 }  // namespace da

@@ -49,5 +49,7 @@ __global__ void k_dot_gt_d(LbfgsArgs a);
 __global__ void k_accept(LbfgsArgs a);
 // scal[GG] = g . g for every member.  grid B.
 __global__ void k_gnorm2(LbfgsArgs a);
+// g = gt for masked members (their first evaluation).  grid (chunks, B).
+__global__ void k_take_gradient(LbfgsArgs a);
 
 }  // namespace da

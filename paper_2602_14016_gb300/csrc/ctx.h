@@ -24,6 +24,21 @@ struct da_ctx {
   da_forcing force{};
   da_obs_operator obs{};
   int nt = 0, P = 0;
+  // ragged batches (da_set_member): per-member windows, end-aligned in each
+  // evaluation's window of eval_steps steps (the longest live member's)
+  bool ragged = false;
+  std::vector<int> m_nsteps, m_px, m_force;
+  std::vector<double> m_nu;
+  int eval_steps = 0;
+  int* d_mstart = nullptr;   // device tables read by the kernels (Dev)
+  int* d_mnt = nullptr;
+  int* d_mpx = nullptr;
+  int* d_mforce = nullptr;
+  double* d_mnu = nullptr;
+  int* d_kind = nullptr;     // member kernels, for re-making the multiplier
+  double *d_param = nullptr, *d_table = nullptr;
+  std::vector<int> h_kind;
+  std::vector<double> h_param;
   const Ops* ops = nullptr;
   Dev dev{};
   std::vector<void*> allocs;
@@ -49,18 +64,40 @@ struct da_ctx {
   double* lb_dargs = nullptr;
   double* lb_host = nullptr;   // pinned mirror of lb_scal and lb_J
   int mem = 0;
-  // CUDA-graph replay of da_cost_grad
+  // optimiser state per member (lbfgs.cu), freed by free_optimiser
+  void* lb_state = nullptr;
+  // CUDA-graph replay of da_cost_grad (captured per evaluation window)
   bool use_graph = false;
-  cudaGraphExec_t cg_exec = nullptr;
-  unsigned long long cg_launches = 0;  // kernel nodes in the captured graph
+  struct CapturedEval {
+    int steps;                    // the evaluation window it was captured for
+    cudaGraphExec_t exec;
+    unsigned long long launches;  // kernel nodes in it
+  };
+  std::vector<CapturedEval> cg_cache;  // newest last, at most kMaxCapturedEvals
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   double *sbuf = nullptr, *gbuf = nullptr;
+  // CUDA-graph replay of da_adjoint_spectra (captured per save_every and outputs)
+  cudaGraphExec_t sp_exec = nullptr;
+  unsigned long long sp_launches = 0;
+  int sp_key = -1;
+  double *sp_lbuf = nullptr, *sp_member = nullptr, *sp_mean = nullptr;
   // event timing of one kernel class
   int timed_class = 0;
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
 };
+
+// Captured evaluations kept per context: one per evaluation window that a
+// ragged batch's live members produce (a window is the longest live horizon).
+constexpr size_t kMaxCapturedEvals = 16;
+
+// Drops every captured evaluation (their kernel arguments or launch sequence
+// changed).
+inline void drop_graphs(da_ctx* c) {
+  for (auto& g : c->cg_cache) cudaGraphExecDestroy(g.exec);
+  c->cg_cache.clear();
+}
 
 // Message of the last failed da_create (no context to hold it).
 extern std::string g_create_error;
@@ -135,12 +172,25 @@ da_status dalloc(da_ctx* c, T** p, size_t count) {
   return DA_OK;
 }
 
-// Observation slot of step k, or -1 (host copy of the kernels' obs_slot).
-inline int obs_slot_host(const da_ctx* c, int k) {
-  if (k == 0) return c->obs.include_t0 ? 0 : -1;
-  if (k % c->obs.every) return -1;
-  return k / c->obs.every - 1 + (c->obs.include_t0 ? 1 : 0);
-}
+// Whether global step k of the evaluation window can be an observation step
+// of some member (every member's window is a whole number of observation
+// intervals and ends with the evaluation's, so its observation steps fall on
+// multiples of obs.every; the kernels find each member's slot).
+inline bool obs_step_host(const da_ctx* c, int k) { return k % c->obs.every == 0; }
+
+// Sets the evaluation window for the members marked in `live` (all members
+// with a non-empty window if live is NULL): eval_steps = the longest live
+// window, each live member end-aligned in it, the others idle; uploads the
+// start table of a ragged batch on stream st.  Homogeneous contexts always
+// evaluate every member over the context's window.
+da_status set_eval_window(da_ctx* c, const std::vector<char>* live, cudaStream_t st);
+
+// Cost and gradient of the members marked in `live` (lbfgs.cu's evaluations).
+da_status cost_grad_members(da_ctx* c, const double* s, double* J, double* grad_s, const std::vector<char>* live,
+                            cudaStream_t st);
+
+// Frees the optimiser state of lbfgs.cu (da_destroy).
+void free_optimiser(da_ctx* c);
 
 // Plan variant the autotuner chose for (n, batch) in this process, or 0
 // (plans.cu).

@@ -81,6 +81,13 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
   d.force = f.kind == DA_FORCE_KOLMOGOROV;
   d.amp = f.amp;
   d.nf = f.nf;
+  d.ragged = 0;
+  d.obs_stride = (size_t)c->nt * c->P * c->P * 2;
+  c->eval_steps = c->nsteps;
+  c->m_nsteps.assign(c->B, c->nsteps);
+  c->m_px.assign(c->B, c->P);
+  c->m_nu.assign(c->B, nu);
+  c->m_force.assign(c->B, d.force);
 
   const size_t B = c->B, N = n, comp = B * ops->Kr * ops->Kc, P2 = (size_t)c->P * c->P;
   da_status s = DA_OK;
@@ -103,10 +110,20 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
   size_t fold_max = 0;  // room for the folded table of any plan variant
   for (int v = 0; v < da::plan_count(n); ++v) fold_max = std::max(fold_max, (size_t)da::ops_for(n, v)->fold_doubles);
   A(dalloc(c, (double**)&d.fold, fold_max));
-  A(dalloc(c, (double2**)&d.twP, (size_t)c->P));
+  A(dalloc(c, (double2**)&d.twP, (size_t)64));
   A(dalloc(c, (da::Sym4**)&d.symF, comp / B));
   A(dalloc(c, (da::Sym4**)&d.symA, comp / B));
-  A(dalloc(c, (double**)&d.nuk2, comp / B));
+  A(dalloc(c, (double**)&d.k2, comp / B));
+  A(dalloc(c, &c->d_mstart, B));
+  A(dalloc(c, &c->d_mnt, B));
+  A(dalloc(c, &c->d_mpx, B));
+  A(dalloc(c, &c->d_mforce, B));
+  A(dalloc(c, &c->d_mnu, B));
+  d.mstart = c->d_mstart;
+  d.mnt = c->d_mnt;
+  d.mpx = c->d_mpx;
+  d.mforce = c->d_mforce;
+  d.mnu = c->d_mnu;
   // stage-field store: the whole window, or one checkpoint segment
   if (c->ckpt == 0) {
     d.traj_steps = c->nsteps;
@@ -116,13 +133,13 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
     A(dalloc(c, &c->ckpt_buf, (size_t)c->nckpt * comp));
   }
   if (c->ckpt >= 0) A(dalloc(c, &d.traj, B * (size_t)d.traj_steps * 8 * N * N));
-  int* d_kind = nullptr;
-  double *d_param = nullptr, *d_table = nullptr;
-  A(dalloc(c, &d_kind, B));
-  A(dalloc(c, &d_param, B));
+  A(dalloc(c, &c->d_kind, B));
+  A(dalloc(c, &c->d_param, B));
   bool any_table = false;
   for (int b = 0; b < c->B; ++b) any_table |= kernels[b].kind == DA_KERNEL_TABLE;
-  if (any_table) A(dalloc(c, &d_table, B * N * (N / 2 + 1)));
+  if (any_table) A(dalloc(c, &c->d_table, B * N * (N / 2 + 1)));
+  int* d_kind = c->d_kind;
+  double *d_param = c->d_param, *d_table = c->d_table;
   if (s != DA_OK) {
     g_create_error = c->err;
     da_destroy(c);
@@ -132,19 +149,21 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
   // lattice
   std::vector<double> fold(ops->fold_doubles);
   ops->fold_table(fold.data());
-  std::vector<double2> twP = roots_of_unity(c->P);
-  std::vector<int> kind(B);
-  std::vector<double> param(B);
+  std::vector<double2> twP = roots_of_unity(64);
+  std::vector<int>& kind = c->h_kind;
+  std::vector<double>& param = c->h_param;
+  kind.resize(B);
+  param.resize(B);
   for (size_t b = 0; b < B; ++b) {
     kind[b] = kernels[b].kind;
     param[b] = kernels[b].param;
   }
   cudaError_t e = cudaMemcpy((void*)d.fold, fold.data(), fold.size() * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy((void*)d.twP, twP.data(), c->P * sizeof(double2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy((void*)d.twP, twP.data(), 64 * sizeof(double2), cudaMemcpyHostToDevice);
   // per-mode symbols of the column passes, column-major [Kc][Kr]
   const int K = ops->K, Kr = ops->Kr, Kc = ops->Kc;
   std::vector<da::Sym4> symF((size_t)Kr * Kc), symA((size_t)Kr * Kc);
-  std::vector<double> nuk2((size_t)Kr * Kc);
+  std::vector<double> k2tab((size_t)Kr * Kc);
   const double s2 = 1.0 / ((double)n * n);
   for (int kx = 0; kx < Kc; ++kx)
     for (int r = 0; r < Kr; ++r) {
@@ -154,11 +173,20 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
       const size_t i = (size_t)kx * Kr + r;
       symF[i] = {ky * ik2 * s2, kx * ik2 * s2, 0.5 * (ky * ky - kx * kx), -0.5 * kx * ky};
       symA[i] = {0.5 * ky * ik2, 0.5 * kx * ik2, -2.0 * kx * ky * s2, (double)(ky * ky - kx * kx) * s2};
-      nuk2[i] = nu * k2;
+      k2tab[i] = k2;
     }
   if (e == cudaSuccess) e = cudaMemcpy((void*)d.symF, symF.data(), symF.size() * sizeof(da::Sym4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy((void*)d.symA, symA.data(), symA.size() * sizeof(da::Sym4), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy((void*)d.nuk2, nuk2.data(), nuk2.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy((void*)d.k2, k2tab.data(), k2tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+  {
+    const std::vector<int> zeros(B, 0), nts(B, c->nt), pxs(B, c->P), forces(B, d.force);
+    const std::vector<double> nus(B, nu);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_mstart, zeros.data(), B * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_mnt, nts.data(), B * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_mpx, pxs.data(), B * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_mforce, forces.data(), B * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_mnu, nus.data(), B * sizeof(double), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemcpy(d_kind, kind.data(), B * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_param, param.data(), B * sizeof(double), cudaMemcpyHostToDevice);
   for (size_t b = 0; b < B && e == cudaSuccess; ++b)
@@ -172,7 +200,7 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
     da_destroy(c);
     return DA_ECUDA;
   }
-  ops->make_mult(d, (double*)d.mult, d_kind, d_param, d_table, nu, 0);
+  ops->make_mult(d, (double*)d.mult, d_kind, d_param, d_table, c->d_mnu, 0);
   c->launches++;
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -217,7 +245,9 @@ extern "C" da_status da_kernel_time(da_ctx* c, double* total_ms, unsigned long l
 
 extern "C" void da_destroy(da_ctx* c) {
   if (!c) return;
-  if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
+  free_optimiser(c);
+  drop_graphs(c);
+  if (c->sp_exec) cudaGraphExecDestroy(c->sp_exec);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->gstream) cudaStreamDestroy(c->gstream);
@@ -239,10 +269,7 @@ extern "C" da_status da_set_sobolev(da_ctx* c, double lambda) {
     if (r) return r;
   }
   c->sobolev = lambda;
-  if (c->cg_exec) {  // the captured sequence depends on the regularisation
-    cudaGraphExecDestroy(c->cg_exec);
-    c->cg_exec = nullptr;
-  }
+  drop_graphs(c);  // the captured sequences depend on the regularisation
   return DA_OK;
 }
 
@@ -262,8 +289,9 @@ static da_status run_forward(da_ctx* c, const double* s, bool gather, cudaStream
   const Ops* o = c->ops;
   Dev& d = c->dev;
   const bool store = d.traj != nullptr;
-  const int K = c->ckpt > 0 ? c->ckpt : c->nsteps;
-  const int last0 = ((c->nsteps - 1) / K) * K;  // first step of the last segment
+  const int E = c->eval_steps;  // the evaluation's window (all of nsteps unless a ragged batch is shorter)
+  const int K = c->ckpt > 0 ? c->ckpt : E;
+  const int last0 = ((E - 1) / K) * K;  // first step of the last segment
   const size_t comp = (size_t)c->B * o->Kr * o->Kc;
   c->have_fwd = false;
   o->r2c_rows(d, s, st);
@@ -273,11 +301,11 @@ static da_status run_forward(da_ctx* c, const double* s, bool gather, cudaStream
   if (c->w0) DA_TRY_CUDA(c, cudaMemcpyAsync(c->w0, d.W, comp * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   d.seg0 = last0;
   if (c->ckpt == 0) d.seg0 = 0;
-  for (int k = 0; k < c->nsteps; ++k) {
+  for (int k = 0; k < E; ++k) {
     if (c->ckpt > 0 && store && k % K == 0)
       DA_TRY_CUDA(c, cudaMemcpyAsync(c->ckpt_buf + (size_t)(k / K) * comp, d.W, comp * sizeof(double2),
                                      cudaMemcpyDeviceToDevice, st));
-    const int obs_flag = (gather && obs_slot_host(c, k) >= 0) ? da::F_OBS : 0;
+    const int obs_flag = (gather && obs_step_host(c, k)) ? da::F_OBS : 0;
     const int store_flag = (store && k >= d.seg0) ? da::F_STORE : 0;
     for (int j = 1; j <= 4; ++j) {
       {
@@ -285,12 +313,12 @@ static da_status run_forward(da_ctx* c, const double* s, bool gather, cudaStream
         o->fwd_rows(d, k, j, store_flag | (j == 1 ? obs_flag : 0), st);
       }
       Timed t(c, 2, st);
-      o->fwd_cols(d, j, 0, st);
+      o->fwd_cols(d, k, j, 0, st);
     }
     if ((r = check_launch(c, 8))) return r;
   }
-  if (gather && obs_slot_host(c, c->nsteps) >= 0) {
-    o->fwd_rows(d, c->nsteps, 1, da::F_OBS_ONLY, st);
+  if (gather && obs_step_host(c, E)) {
+    o->fwd_rows(d, E, 1, da::F_OBS_ONLY, st);
     if ((r = check_launch(c))) return r;
   }
   c->have_fwd = store;
@@ -338,12 +366,13 @@ static da_status record_spectra(da_ctx* c, const SpectraOut* sp, int k, cudaStre
 static da_status run_adjoint(da_ctx* c, bool sources, cudaStream_t st, const SpectraOut* sp = nullptr) {
   const Ops* o = c->ops;
   Dev& d = c->dev;
-  const int K = c->ckpt > 0 ? c->ckpt : c->nsteps;
-  const int nseg = (c->nsteps + K - 1) / K;
+  const int E = c->eval_steps;
+  const int K = c->ckpt > 0 ? c->ckpt : E;
+  const int nseg = (E + K - 1) / K;
   const size_t comp = (size_t)c->B * o->Kr * o->Kc;
   da_status r;
   for (int seg = nseg - 1; seg >= 0; --seg) {
-    const int k0 = seg * K, k1 = std::min(k0 + K, c->nsteps);
+    const int k0 = seg * K, k1 = std::min(k0 + K, E);
     if (seg != nseg - 1) {
       DA_TRY_CUDA(c, cudaMemcpyAsync(d.W, c->ckpt_buf + (size_t)seg * comp, comp * sizeof(double2),
                                      cudaMemcpyDeviceToDevice, st));
@@ -357,7 +386,7 @@ static da_status run_adjoint(da_ctx* c, bool sources, cudaStream_t st, const Spe
             o->fwd_rows(d, k, j, da::F_STORE, st);
           }
           Timed t(c, 2, st);
-          o->fwd_cols(d, j, 0, st);
+          o->fwd_cols(d, k, j, 0, st);
         }
         if ((r = check_launch(c, 8))) return r;
       }
@@ -367,9 +396,7 @@ static da_status run_adjoint(da_ctx* c, bool sources, cudaStream_t st, const Spe
     d.seg0 = k0;
     for (int k = k1 - 1; k >= k0; --k) {
       for (int j = 4; j >= 1; --j) {
-        int flags = 0;
-        if (j == 1 && sources && obs_slot_host(c, k) >= 0) flags |= da::F_SRC;
-        if (j == 1 && k == 0) flags |= da::F_FINAL;
+        const int flags = (j == 1 && sources && obs_step_host(c, k)) ? da::F_SRC : 0;
         {
           Timed t(c, 3, st);
           o->adj_rows(d, k, j, st);
@@ -407,10 +434,110 @@ static da_status gradient_out(da_ctx* c, double* grad_s, cudaStream_t st) {
   return check_launch(c, 2);
 }
 
+da_status set_eval_window(da_ctx* c, const std::vector<char>* live, cudaStream_t st) {
+  if (!c->ragged) {
+    c->eval_steps = c->nsteps;
+    c->dev.nsteps = c->nsteps;
+    return DA_OK;
+  }
+  int E = 0;
+  for (int b = 0; b < c->B; ++b)
+    if ((!live || (*live)[b]) && c->m_nsteps[b] > 0) E = std::max(E, c->m_nsteps[b]);
+  if (E == 0) E = c->obs.every;  // nothing live: a minimal window over idle members
+  std::vector<int> start(c->B);
+  for (int b = 0; b < c->B; ++b) {
+    const bool on = (!live || (*live)[b]) && c->m_nsteps[b] > 0;
+    start[b] = on ? E - c->m_nsteps[b] : E + 1;  // idle: later than the window's last step
+  }
+  DA_TRY_CUDA(c, cudaMemcpyAsync(c->d_mstart, start.data(), c->B * sizeof(int), cudaMemcpyHostToDevice, st));
+  c->eval_steps = E;
+  c->dev.nsteps = E;
+  return DA_OK;
+}
+
+extern "C" da_status da_set_member(da_ctx* c, int member, const da_member_window* w, const da_kernel* kernel,
+                                   const double* m, void* stream) {
+  if (!c || !w) return fail(c, DA_EINVAL, "ctx and w must not be NULL");
+  if (member < 0 || member >= c->B) return fail(c, DA_EINVAL, "member out of range");
+  if (w->nsteps < 0 || w->nsteps > c->nsteps || w->nsteps % c->obs.every)
+    return fail(c, DA_EINVAL, "member nsteps must be a multiple of obs.every in [0, the context's nsteps]");
+  if (w->nsteps > 0) {
+    if (w->px < 1 || w->px > c->P || c->n % w->px)
+      return fail(c, DA_EINVAL, "member px must divide n and be at most the context's px");
+    if (!(w->nu >= 0.0) || !std::isfinite(w->nu)) return fail(c, DA_EINVAL, "member nu must be finite and >= 0");
+    if (w->forcing != 0 && w->forcing != 1) return fail(c, DA_EINVAL, "member forcing must be 0 or 1");
+    if (w->forcing && !c->dev.force) return fail(c, DA_EINVAL, "member forcing needs a context created with forcing");
+    if (!kernel) return fail(c, DA_EINVAL, "kernel must not be NULL");
+    if (kernel->kind < DA_KERNEL_IDENTITY || kernel->kind > DA_KERNEL_TABLE || !std::isfinite(kernel->param))
+      return fail(c, DA_EINVAL, "unknown kernel kind or non-finite parameter");
+    if (kernel->kind == DA_KERNEL_TABLE && !kernel->table) return fail(c, DA_EINVAL, "table kernel needs a table");
+    if (!m) return fail(c, DA_EINVAL, "observations must not be NULL");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = c->n;
+  const int nt = w->nsteps > 0 ? w->nsteps / c->obs.every + (c->obs.include_t0 ? 1 : 0) : 0;
+  // work in flight may read the member's tables, multiplier and data
+  DA_TRY_CUDA(c, cudaStreamSynchronize(st));
+  if (w->nsteps > 0) {
+    if (kernel->kind == DA_KERNEL_TABLE) {
+      if (!c->d_table) {
+        da_status r = dalloc(c, &c->d_table, (size_t)c->B * n * (n / 2 + 1));
+        if (r) return r;
+      }
+      DA_TRY_CUDA(c, cudaMemcpy(c->d_table + (size_t)member * n * (n / 2 + 1), kernel->table,
+                                (size_t)n * (n / 2 + 1) * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    const int kind = kernel->kind;
+    const double param = kernel->param;
+    DA_TRY_CUDA(c, cudaMemcpy(c->d_kind + member, &kind, sizeof(int), cudaMemcpyHostToDevice));
+    DA_TRY_CUDA(c, cudaMemcpy(c->d_param + member, &param, sizeof(double), cudaMemcpyHostToDevice));
+    // the multiplier of every member with its kernel and viscosity; this
+    // member's must be finite and non-negative on the retained set
+    DA_TRY_CUDA(c, cudaMemcpy(c->d_mnu + member, &w->nu, sizeof(double), cudaMemcpyHostToDevice));
+    c->ops->make_mult(c->dev, (double*)c->dev.mult, c->d_kind, c->d_param, c->d_table, c->d_mnu, 0);
+    da_status r = check_launch(c);
+    if (r) return r;
+    const size_t nm = (size_t)c->ops->Kr * c->ops->Kc;
+    std::vector<double> mult(nm);
+    DA_TRY_CUDA(c, cudaMemcpy(mult.data(), c->dev.mult + member * nm, nm * sizeof(double), cudaMemcpyDeviceToHost));
+    for (double v : mult)
+      if (!std::isfinite(v) || v < 0.0) {
+        c->m_nsteps[member] = 0;  // the slot stays idle
+        return fail(c, DA_EINVAL, "kernel W is not finite and non-negative on the retained set");
+      }
+    c->h_kind[member] = kind;
+    c->h_param[member] = param;
+    const size_t cnt = (size_t)nt * w->px * w->px * 2;
+    DA_TRY_CUDA(c, cudaMemcpyAsync((void*)(c->dev.mobs + member * c->dev.obs_stride), m, cnt * sizeof(double),
+                                   cudaMemcpyDefault, st));
+    c->m_px[member] = w->px;
+    c->m_nu[member] = w->nu;
+    c->m_force[member] = w->forcing;
+  }
+  c->m_nsteps[member] = w->nsteps;
+  const int px = c->m_px[member], force = c->m_force[member];
+  const double nu = c->m_nu[member];
+  DA_TRY_CUDA(c, cudaMemcpy(c->d_mnt + member, &nt, sizeof(int), cudaMemcpyHostToDevice));
+  DA_TRY_CUDA(c, cudaMemcpy(c->d_mpx + member, &px, sizeof(int), cudaMemcpyHostToDevice));
+  DA_TRY_CUDA(c, cudaMemcpy(c->d_mforce + member, &force, sizeof(int), cudaMemcpyHostToDevice));
+  DA_TRY_CUDA(c, cudaMemcpy(c->d_mnu + member, &nu, sizeof(double), cudaMemcpyHostToDevice));
+  if (!c->ragged) {
+    drop_graphs(c);  // captured sequences hold the homogeneous kernel arguments
+    c->ragged = true;
+    c->dev.ragged = 1;
+    c->have_obs = true;  // the other members keep the observations they had (or zeros)
+  }
+
+  c->have_fwd = false;
+  return DA_OK;
+}
+
 extern "C" da_status da_forward(da_ctx* c, const double* s, double* omegaT, double* obs, void* stream) {
   if (!c || !s) return fail(c, DA_EINVAL, "ctx and s must not be NULL");
   cudaStream_t st = (cudaStream_t)stream;
-  da_status r = run_forward(c, s, obs != nullptr, st);
+  da_status r = set_eval_window(c, nullptr, st);
+  if (r) return r;
+  r = run_forward(c, s, obs != nullptr, st);
   if (r) return r;
   if (omegaT) {
     c->ops->compact_to_half(c->dev, c->dev.W, (double2*)omegaT, st);
@@ -465,17 +592,25 @@ extern "C" da_status da_cost_grad(da_ctx* c, const double* s, double* J, double*
   if (!c || !s) return fail(c, DA_EINVAL, "ctx and s must not be NULL");
   if (!c->have_obs) return fail(c, DA_EINVAL, "no observations: call da_set_observations first");
   if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
-  cudaStream_t st = (cudaStream_t)stream;
-  da_status r;
+  return cost_grad_members(c, s, J, grad_s, nullptr, (cudaStream_t)stream);
+}
+
+da_status cost_grad_members(da_ctx* c, const double* s, double* J, double* grad_s, const std::vector<char>* live,
+                            cudaStream_t st) {
+  da_status r = set_eval_window(c, live, st);
+  if (r) return r;
   if (c->use_graph && c->timed_class == 0) {
-    // replay one captured evaluation on the context's stream, ordered after
-    // and before the caller's stream by events
+    // one captured sequence per evaluation window (its launch count)
     const size_t bytes = (size_t)c->B * c->n * c->n * sizeof(double);
     DA_TRY_CUDA(c, cudaMemcpyAsync(c->sbuf, s, bytes, cudaMemcpyDeviceToDevice, st));
     DA_TRY_CUDA(c, cudaEventRecord(c->ev_in, st));
     DA_TRY_CUDA(c, cudaStreamWaitEvent(c->gstream, c->ev_in, 0));
-    if (!c->cg_exec) {
+    da_ctx::CapturedEval* ce = nullptr;
+    for (auto& g : c->cg_cache)
+      if (g.steps == c->eval_steps) ce = &g;
+    if (!ce) {
       cudaGraph_t g = nullptr;
+      cudaGraphExec_t ex = nullptr;
       const unsigned long long l0 = c->launches;
       DA_TRY_CUDA(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
       r = enqueue_cost_grad(c, c->sbuf, c->gbuf, c->gstream);
@@ -485,17 +620,19 @@ extern "C" da_status da_cost_grad(da_ctx* c, const double* s, double* J, double*
         return r;
       }
       if (e != cudaSuccess) return fail(c, DA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&c->cg_exec, g, 0);
+      e = cudaGraphInstantiate(&ex, g, 0);
       cudaGraphDestroy(g);
-      if (e != cudaSuccess) {
-        c->cg_exec = nullptr;
-        return fail(c, DA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      if (e != cudaSuccess) return fail(c, DA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      if (c->cg_cache.size() >= kMaxCapturedEvals) {  // evict the oldest
+        cudaGraphExecDestroy(c->cg_cache.front().exec);
+        c->cg_cache.erase(c->cg_cache.begin());
       }
-      c->cg_launches = c->launches - l0;
+      c->cg_cache.push_back({c->eval_steps, ex, c->launches - l0});
       c->launches = l0;
+      ce = &c->cg_cache.back();
     }
-    DA_TRY_CUDA(c, cudaGraphLaunch(c->cg_exec, c->gstream));
-    c->launches += c->cg_launches;
+    DA_TRY_CUDA(c, cudaGraphLaunch(ce->exec, c->gstream));
+    c->launches += ce->launches;
     c->have_fwd = c->ckpt == 0;
     DA_TRY_CUDA(c, cudaEventRecord(c->ev_out, c->gstream));
     DA_TRY_CUDA(c, cudaStreamWaitEvent(st, c->ev_out, 0));
@@ -511,7 +648,9 @@ extern "C" da_status da_adjoint_terminal(da_ctx* c, const double* s, const doubl
   if (!c || !s || !lamT) return fail(c, DA_EINVAL, "ctx, s and lamT must not be NULL");
   if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
   cudaStream_t st = (cudaStream_t)stream;
-  da_status r = run_forward(c, s, false, st);
+  da_status r = set_eval_window(c, nullptr, st);
+  if (r) return r;
+  r = run_forward(c, s, false, st);
   if (r) return r;
   c->ops->half_to_compact(c->dev, (const double2*)lamT, c->dev.LamBar, st);
   c->ops->adj_init(c->dev, da::INIT_LAMBAR, st);
@@ -584,28 +723,92 @@ static da_status build_shells(da_ctx* c) {
 
 extern "C" int da_num_shells(const da_ctx* c) { return c ? (int)std::floor(std::sqrt(2.0) * c->ops->K) + 1 : 0; }
 
+// The launch sequence of da_adjoint_spectra on stream st (buffers set up).
+static da_status enqueue_spectra(da_ctx* c, const double* s, const double* lamT, const SpectraOut& sp,
+                                 cudaStream_t st) {
+  da_status r = run_forward(c, s, false, st);
+  if (r) return r;
+  c->ops->half_to_compact(c->dev, (const double2*)lamT, c->dev.LamBar, st);
+  c->ops->adj_init(c->dev, da::INIT_LAMBAR, st);
+  if ((r = check_launch(c, 2))) return r;
+  if ((r = record_spectra(c, &sp, c->nsteps, st))) return r;
+  return run_adjoint(c, false, st, &sp);
+}
+
 extern "C" da_status da_adjoint_spectra(da_ctx* c, const double* s, const double* lamT, int save_every,
                                         double* member, double* mean, void* stream) {
   if (!c || !s || !lamT) return fail(c, DA_EINVAL, "ctx, s and lamT must not be NULL");
   if (save_every < 1 || c->nsteps % save_every) return fail(c, DA_EINVAL, "save_every must divide nsteps");
   if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
+  if (c->ragged) return fail(c, DA_EINVAL, "adjoint spectra need every member on the context's window");
   da_status r = build_shells(c);
   if (r) return r;
   cudaStream_t st = (cudaStream_t)stream;
-  SpectraOut sp;
-  sp.every = save_every;
-  sp.member = member;
-  sp.mean = mean;
   if (member && !c->shell_scratch) {
     if ((r = dalloc(c, &c->shell_scratch, (size_t)c->B * c->nshell))) return r;
   }
+  SpectraOut sp;
+  sp.every = save_every;
   sp.scratch = c->shell_scratch;
-  if ((r = run_forward(c, s, false, st))) return r;
-  c->ops->half_to_compact(c->dev, (const double2*)lamT, c->dev.LamBar, st);
-  c->ops->adj_init(c->dev, da::INIT_LAMBAR, st);
-  if ((r = check_launch(c, 2))) return r;
-  if ((r = record_spectra(c, &sp, c->nsteps, st))) return r;
-  if ((r = run_adjoint(c, false, st, &sp))) return r;
+  if (!(c->use_graph && c->timed_class == 0)) {
+    sp.member = member;
+    sp.mean = mean;
+    if ((r = enqueue_spectra(c, s, lamT, sp, st))) return r;
+    c->have_adj = true;
+    return DA_OK;
+  }
+  // graph replay: inputs copied into and outputs out of internal buffers,
+  // the sequence captured once per (save_every, outputs asked for)
+  const int nsave = c->nsteps / save_every + 1;
+  const int key = save_every * 4 + (member ? 2 : 0) + (mean ? 1 : 0);
+  const size_t sbytes = (size_t)c->B * c->n * c->n * sizeof(double);
+  const size_t lbytes = (size_t)c->B * c->n * (c->n / 2 + 1) * 2 * sizeof(double);
+  if (!c->sp_lbuf && (r = dalloc(c, &c->sp_lbuf, lbytes / sizeof(double)))) return r;
+  if (c->sp_key != key) {
+    if (c->sp_exec) cudaGraphExecDestroy(c->sp_exec);
+    c->sp_exec = nullptr;
+    c->sp_member = c->sp_mean = nullptr;
+    if (member && (r = dalloc(c, &c->sp_member, (size_t)c->B * nsave * c->nshell))) return r;
+    if (mean && (r = dalloc(c, &c->sp_mean, (size_t)nsave * c->nshell))) return r;
+    c->sp_key = key;
+  }
+  sp.member = c->sp_member;
+  sp.mean = c->sp_mean;
+  DA_TRY_CUDA(c, cudaMemcpyAsync(c->sbuf, s, sbytes, cudaMemcpyDeviceToDevice, st));
+  DA_TRY_CUDA(c, cudaMemcpyAsync(c->sp_lbuf, lamT, lbytes, cudaMemcpyDeviceToDevice, st));
+  DA_TRY_CUDA(c, cudaEventRecord(c->ev_in, st));
+  DA_TRY_CUDA(c, cudaStreamWaitEvent(c->gstream, c->ev_in, 0));
+  if (!c->sp_exec) {
+    cudaGraph_t g = nullptr;
+    const unsigned long long l0 = c->launches;
+    DA_TRY_CUDA(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+    r = enqueue_spectra(c, c->sbuf, c->sp_lbuf, sp, c->gstream);
+    cudaError_t e = cudaStreamEndCapture(c->gstream, &g);
+    if (r) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (e != cudaSuccess) return fail(c, DA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->sp_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->sp_exec = nullptr;
+      return fail(c, DA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    c->sp_launches = c->launches - l0;
+    c->launches = l0;
+  }
+  DA_TRY_CUDA(c, cudaGraphLaunch(c->sp_exec, c->gstream));
+  c->launches += c->sp_launches;
+  c->have_fwd = c->ckpt == 0;
+  DA_TRY_CUDA(c, cudaEventRecord(c->ev_out, c->gstream));
+  DA_TRY_CUDA(c, cudaStreamWaitEvent(st, c->ev_out, 0));
+  if (member)
+    DA_TRY_CUDA(c, cudaMemcpyAsync(member, c->sp_member, (size_t)c->B * nsave * c->nshell * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st));
+  if (mean)
+    DA_TRY_CUDA(c, cudaMemcpyAsync(mean, c->sp_mean, (size_t)nsave * c->nshell * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st));
   c->have_adj = true;
   return DA_OK;
 }

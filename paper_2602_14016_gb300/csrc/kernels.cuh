@@ -43,8 +43,7 @@ enum : int {
   F_OBS = 2,       // forward row pass: gather probes into the observation slot
   F_OBS_ONLY = 4,  // forward row pass: only gather probes (final state)
   F_NO_NEXT = 8,   // column pass: skip the inverse transforms of the next stage
-  F_SRC = 16,      // adjoint column pass: add the observation source at this step
-  F_FINAL = 32     // adjoint column pass: last step (lambda_0 stays in LamBar)
+  F_SRC = 16       // adjoint column pass: add the observation source at this step
 };
 
 // Start of the adjoint sweep (k_adj_init): add the observation source of
@@ -64,18 +63,30 @@ enum : int { M_ONE = 0, M_CTRL = 1, M_FILTERED = 2, M_INV_CTRL = 3 };
 //   adj: a1 = ky/k^2/2, c1 = kx/k^2/2 (transposed velocity symbols, same
 //        1/2), ca = -2 kx ky/N^2, cb = (ky^2 - kx^2)/N^2 (adjoint-field
 //        columns; ca carries the 2 of rho_u, rho_v);
-//   nuk2 = nu k^2.
+//   k2 = k^2 (the column passes multiply it by the member's viscosity).
 struct __align__(32) Sym4 {
   double a, b, c, d;
 };
 
 // Everything a kernel needs, passed by value.
 struct Dev {
-  int B, nsteps, every, include_t0, px, nt;
+  int B, nsteps, every, include_t0, px, nt;  // nsteps: the evaluation's window (global steps)
   double dt, nu;
   int force;
   double amp;
   int nf;
+  // Ragged batches: member b runs its own window, end-aligned in the
+  // evaluation's -- live from global step mstart[b] to nsteps, its local step
+  // n - mstart[b] -- with its own probe lattice, viscosity and forcing switch;
+  // a member with mstart[b] > nsteps is idle.  With ragged == 0 every member
+  // runs the context's window and the tables are not read.
+  int ragged;
+  const int* mstart;                         // [B]
+  const int* mnt;                            // [B] observation times of member b
+  const int* mpx;                            // [B] probes per side of member b
+  const double* mnu;                         // [B]
+  const int* mforce;                         // [B] Kolmogorov forcing on (1) or off (0)
+  size_t obs_stride;                         // doubles from one member's obs, mobs, res to the next
   double2 *W, *Acc, *Y, *KB, *LamBar, *Sum;  // compact [B][Kc][Kr] (cidx)
   double2* Mx;                               // mixed [B][2][N][Kc]: column-pass output
   double2* Mn;                               // mixed [B][2][N][Kc]: row-pass output
@@ -88,10 +99,10 @@ struct Dev {
   double* J;                                 // [B]
   const double* mult;                        // control multiplier |k| W^1/2, compact [B][Kc][Kr]
   const double* fold;                        // folded twiddles of Plan<N> (fft.cuh)
-  const double2* twP;                        // W_P^t, t < P
+  const double2* twP;                        // W_64^t, t < 64 (W_P^t = W_64^{t 64/P})
   const Sym4* symF;                          // [Kc][Kr] su, sv, cp, cq
   const Sym4* symA;                          // [Kc][Kr] a1, c1, ca, cb
-  const double* nuk2;                        // [Kc][Kr] nu k^2
+  const double* k2;                          // [Kc][Kr] k^2 (times nu of the member)
   double dt2, dt3, dt6;                      // dt/2, dt/3, dt/6
 };
 
@@ -125,7 +136,19 @@ __device__ __forceinline__ void load_fold(double* T, const double* __restrict__ 
   for (int i = threadIdx.x; i < FoldInfo<N, V>::DOUBLES; i += blockDim.x) T[i] = g[i];
 }
 
-// Observation slot of step k, or -1.
+// The window of member bm in this evaluation (see Dev).
+struct MemberWindow {
+  int start, P;
+  double nu;
+  bool forced;
+};
+
+__device__ __forceinline__ MemberWindow member_window(const Dev& d, int bm) {
+  if (!d.ragged) return {0, d.px, d.nu, d.force != 0};
+  return {d.mstart[bm], d.mpx[bm], d.mnu[bm], d.force != 0 && d.mforce[bm] != 0};
+}
+
+// Observation slot of local step k, or -1.
 __device__ __forceinline__ int obs_slot(const Dev& d, int k) {
   if (k == 0) return d.include_t0 ? 0 : -1;
   if (k % d.every) return -1;
@@ -465,12 +488,14 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_rows(Dev d, int n, i
   double* T = reinterpret_cast<double*>(sm);
   double2* a = sm + FoldInfo<N, V>::PADDED / 2;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
+  const MemberWindow mw = member_window(d, bm);
+  if (n < mw.start) return;  // the member's window has not begun
   load_fold<N, V>(T, d.fold);
   pack_field_pairs<N, V>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
   __syncthreads();
   fft_folded<N, V, +1, 2>(a, T);
-  const int st = N / d.px;
-  const int slot = (flags & (F_OBS | F_OBS_ONLY)) ? obs_slot(d, n) : -1;
+  const int P = mw.P, st = N / P;
+  const int slot = (flags & (F_OBS | F_OBS_ONLY)) ? obs_slot(d, n - mw.start) : -1;
   double* trj = (flags & F_STORE)
                     ? d.traj + (((size_t)bm * d.traj_steps + (n - d.seg0)) * 4 + (stage - 1)) * 2 * (size_t)N * N
                     : nullptr;
@@ -489,8 +514,8 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_rows(Dev d, int n, i
         trj[(size_t)N * N + o] = uv.y;
       }
       if (slot >= 0 && (y % st) == 0 && (x % st) == 0) {
-        const int p = (y / st) * d.px + x / st;
-        double* o = d.obs + (((size_t)bm * d.nt + slot) * d.px * d.px + p) * 2;
+        const int p = (y / st) * P + x / st;
+        double* o = d.obs + bm * d.obs_stride + ((size_t)slot * P * P + p) * 2;
         o[0] = uv.x;
         o[1] = uv.y;
       }
@@ -512,12 +537,14 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_rows(Dev d, int n, i
 // transforms of u and v of the next stage state.  Acc holds k1 + 2 k2 +
 // 2 k3 (+ k4).  grid (Kc, B).
 template <int N, int V = 0>
-__global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_cols(Dev d, int stage, int flags) {
+__global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_cols(Dev d, int n, int stage, int flags) {
   using G = Geo<N, V>;
   extern __shared__ double2 sm[];
   double* T = reinterpret_cast<double*>(sm);
   double2* a = sm + FoldInfo<N, V>::PADDED / 2;
   const int kx = blockIdx.x, bm = blockIdx.y;
+  const MemberWindow mw = member_window(d, bm);
+  if (n < mw.start) return;
   load_fold<N, V>(T, d.fold);
   load_column<N, G::THREADS, 2>(a, d.Mn + (size_t)bm * 2 * N * G::Kc + kx);
   // the epilogue's inputs for this thread's modes; where registers allow
@@ -535,7 +562,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_cols(Dev d, int stag
       wv[t] = d.W[idx];
       accv[t] = stage > 1 ? d.Acc[idx] : make_double2(0.0, 0.0);
       f[t] = d.symF[kx * G::Kr + rr];
-      nk2[t] = d.nuk2[kx * G::Kr + rr];
+      nk2[t] = mw.nu * d.k2[kx * G::Kr + rr];
     }
   };
   if constexpr (G::PREFETCH) {
@@ -560,7 +587,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_cols(Dev d, int stag
     // F = -(cp P + cq Q) - nu k^2 y
     double2 F = make_double2(-fma(f[t].c, ph.x, fma(f[t].d, qh.x, nk2[t] * yv[t].x)),
                              -fma(f[t].c, ph.y, fma(f[t].d, qh.y, nk2[t] * yv[t].y)));
-    if (d.force && kx == 0 && (ky == d.nf || ky == -d.nf)) F.x += fval;
+    if (mw.forced && kx == 0 && (ky == d.nf || ky == -d.nf)) F.x += fval;
     const double2 w = wv[t], acc = accv[t];
     double2 ynext;
     if (stage == 1) {
@@ -620,13 +647,14 @@ __global__ void k_sobolev_grad(double2* lam, const double2* w0, double lambda, i
 // Separable DFT of the residual at observation slot `slot` on the probe
 // lattice: for each lattice row, T(kx) = sum_q r[row][q] W_P^{kx q}; the
 // column pass then sums over rows with W_P^{ky row}.  Fills Tu, Tv [P].
-__device__ __forceinline__ void probe_row_sums(const Dev& d, int bm, int slot, int kx, double2* Tu, double2* Tv) {
-  const int P = d.px;
-  const double* r = d.res + ((size_t)bm * d.nt + slot) * P * P * 2;
+__device__ __forceinline__ void probe_row_sums(const Dev& d, int bm, int P, int slot, int kx, double2* Tu,
+                                               double2* Tv) {
+  const double* r = d.res + bm * d.obs_stride + (size_t)slot * P * P * 2;
+  const int tws = 64 / P;
   for (int row = threadIdx.x; row < P; row += blockDim.x) {
     double2 su = make_double2(0.0, 0.0), sv = make_double2(0.0, 0.0);
     for (int qq = 0; qq < P; ++qq) {
-      const double2 w = d.twP[(kx * qq) % P];
+      const double2 w = d.twP[((kx * qq) % P) * tws];
       const double ru = r[(row * P + qq) * 2], rv = r[(row * P + qq) * 2 + 1];
       su = make_double2(fma(ru, w.x, su.x), fma(ru, w.y, su.y));
       sv = make_double2(fma(rv, w.x, sv.x), fma(rv, w.y, sv.y));
@@ -638,12 +666,13 @@ __device__ __forceinline__ void probe_row_sums(const Dev& d, int bm, int slot, i
 
 // H^T r at (kx, ky): (-i ky/k^2) R_u + (i kx/k^2) R_v with R the DFT of the
 // probe residual scattered onto the grid.
-__device__ __forceinline__ double2 probe_source(const Dev& d, int kx, int ky, const double2* Tu, const double2* Tv) {
-  const int P = d.px;
+__device__ __forceinline__ double2 probe_source(const Dev& d, int P, int kx, int ky, const double2* Tu,
+                                                const double2* Tv) {
   double2 Ru = make_double2(0.0, 0.0), Rv = make_double2(0.0, 0.0);
   const int kyp = ((ky % P) + P) % P;
+  const int tws = 64 / P;
   for (int row = 0; row < P; ++row) {
-    const double2 w = d.twP[(kyp * row) % P];
+    const double2 w = d.twP[((kyp * row) % P) * tws];
     Ru = cadd(Ru, cmul(Tu[row], w));
     Rv = cadd(Rv, cmul(Tv[row], w));
   }
@@ -667,9 +696,12 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_init(Dev d, int mode
   double2 *a = sm + FoldInfo<N, V>::PADDED / 2, *Tu = a + 2 * N, *Tv = Tu + G::PMAX;
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_fold<N, V>(T, d.fold);
+  const MemberWindow mw = member_window(d, bm);
+  // an idle member starts (and stays) at lambda = 0
+  if (mw.start > d.nsteps) mode = 0;
   const bool resume = (mode & INIT_RESUME) != 0;
-  const int slot = (!resume && (mode & INIT_SRC)) ? obs_slot(d, d.nsteps) : -1;
-  if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
+  const int slot = (!resume && (mode & INIT_SRC)) ? obs_slot(d, d.nsteps - mw.start) : -1;
+  if (slot >= 0) probe_row_sums(d, bm, mw.P, slot, kx, Tu, Tv);
   zero_outside<N>(a, 2);
   __syncthreads();
   #pragma unroll
@@ -681,7 +713,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_init(Dev d, int mode
       kb = d.KB[idx];
     } else {
       double2 lam = (mode & INIT_LAMBAR) ? d.LamBar[idx] : make_double2(0.0, 0.0);
-      if (slot >= 0) lam = cadd(lam, probe_source(d, kx, ky, Tu, Tv));
+      if (slot >= 0) lam = cadd(lam, probe_source(d, mw.P, kx, ky, Tu, Tv));
       d.LamBar[idx] = lam;
       kb = cscale(lam, d.dt6);
       d.KB[idx] = kb;
@@ -704,6 +736,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_rows(Dev d, int n, i
   double* T = reinterpret_cast<double*>(sm);
   double2* a = sm + FoldInfo<N, V>::PADDED / 2;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
+  if (d.ragged && n < d.mstart[bm]) return;
   load_fold<N, V>(T, d.fold);
   pack_field_pairs<N, V>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
   __syncthreads();
@@ -742,6 +775,8 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_cols(Dev d, int n, i
   double* T = reinterpret_cast<double*>(sm);
   double2 *a = sm + FoldInfo<N, V>::PADDED / 2, *Tu = a + 2 * N, *Tv = Tu + G::PMAX;
   const int kx = blockIdx.x, bm = blockIdx.y;
+  const MemberWindow mw = member_window(d, bm);
+  if (n < mw.start) return;
   load_fold<N, V>(T, d.fold);
   load_column<N, G::THREADS, 2>(a, d.Mn + (size_t)bm * 2 * N * G::Kc + kx);
   // the epilogue's inputs for this thread's modes (before the column
@@ -758,15 +793,15 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_cols(Dev d, int n, i
       lbv[t] = d.LamBar[idx];
       sumv[t] = stage < 4 ? d.Sum[idx] : make_double2(0.0, 0.0);
       g[t] = d.symA[kx * G::Kr + rr];
-      nk2[t] = d.nuk2[kx * G::Kr + rr];
+      nk2[t] = mw.nu * d.k2[kx * G::Kr + rr];
     }
   };
   if constexpr (G::PREFETCH) {
 #pragma unroll
     for (int t = 0; t < MT; ++t) load_inputs(t);
   }
-  const int slot = (flags & F_SRC) ? obs_slot(d, n) : -1;
-  if (slot >= 0) probe_row_sums(d, bm, slot, kx, Tu, Tv);
+  const int slot = (flags & F_SRC) ? obs_slot(d, n - mw.start) : -1;
+  if (slot >= 0) probe_row_sums(d, bm, mw.P, slot, kx, Tu, Tv);
   __syncthreads();
   fft_folded<N, V, -1, 2>(a, T);
   const double dt = d.dt;
@@ -800,14 +835,14 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_cols(Dev d, int n, i
     } else {
       const double2 sum = cadd(sumv[t], yb);
       double2 lam = cadd(lb, sum);
-      if (slot >= 0) lam = cadd(lam, probe_source(d, kx, ky, Tu, Tv));
+      if (slot >= 0) lam = cadd(lam, probe_source(d, mw.P, kx, ky, Tu, Tv));
       d.LamBar[idx] = lam;
       nk = cscale(lam, d.dt6);
     }
     d.KB[idx] = nk;
     put_adjoint_columns<N>(a, qi, g[t], nk);
   }
-  if (flags & F_FINAL) return;
+  if (stage == 1 && n == mw.start) return;  // the member's first step: lambda_0 stays in LamBar
   zero_outside<N>(a, 2);
   __syncthreads();
   fft_folded<N, V, +1, 2>(a, T);
@@ -818,7 +853,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_cols(Dev d, int n, i
 // per member.  grid (ceil(Kr*Kc/256), B), block 256.
 template <int N, int V = 0>
 __global__ void k_make_mult(double* __restrict__ mult, const int* __restrict__ kind, const double* __restrict__ param,
-                            const double* __restrict__ table, double nu) {
+                            const double* __restrict__ table, const double* __restrict__ nu) {
   using G = Geo<N, V>;
   const int bm = blockIdx.y;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < G::Kr * G::Kc; i += gridDim.x * blockDim.x) {
@@ -832,7 +867,7 @@ __global__ void k_make_mult(double* __restrict__ mult, const int* __restrict__ k
       case 0: W = 1.0; break;
       case 1: W = exp(-a * k); break;
       case 2: W = pow(k, -2.0 * a); break;
-      case 3: W = exp(-nu * a * k2); break;
+      case 3: W = exp(-nu[bm] * a * k2); break;
       default: W = table[((size_t)bm * N + (ky & (N - 1))) * G::NH + kx]; break;
     }
     mult[(size_t)bm * G::Kr * G::Kc + i] = (kx == 0 && ky == 0) ? 0.0 : k * sqrt(W);

@@ -1,6 +1,8 @@
-// lbfgs.cu -- da_assimilate of include/da.h: L-BFGS on the control, with
-// the cost and gradient of da_cost_grad and the strong-Wolfe line search of
-// linesearch.h; vector operations run in the kernels of blas.cuh.
+// lbfgs.cu -- the optimiser of include/da.h: da_assimilate and the stepwise
+// da_lbfgs_* calls.  L-BFGS on the control (Sec. II.C: L-BFGS on the
+// transformed control in the Euclidean metric), with the cost and gradient
+// of da_cost_grad and the strong-Wolfe line search of linesearch.h; vector
+// operations run in the kernels of blas.cuh.
 #include <algorithm>
 
 #include "blas.cuh"
@@ -8,32 +10,54 @@
 #include "linesearch.h"
 
 // ---------------------------------------------------------------------------
-// L-BFGS driver (Sec. II.C: L-BFGS on the transformed control in the
-// Euclidean metric).  Members advance in lockstep: every cost-gradient
-// evaluation serves all members, and a member that is not searching
-// re-evaluates its accepted point, which changes nothing.  Each member keeps
-// a ring of memory+1 vector slots for its (s, y) pairs, so a new pair can be
-// formed and tested before the oldest one is dropped.
+// Every member slot of a batch has its own optimiser state.  A member is
+// started on a control (da_lbfgs_start), then each round (da_lbfgs_iterate)
+// runs one L-BFGS iteration of every iterating member in lockstep: the
+// members share every cost-gradient evaluation, and a member that is not
+// searching is left out of it (in a ragged batch its CTAs return at once) or,
+// in a homogeneous batch, re-evaluates its accepted point, which changes
+// nothing.  A member started since the last round gets its first evaluation
+// in the round's first evaluation and iterates from the next round, so the
+// arithmetic of a member does not depend on when it joined or who else is in
+// the batch.  Each member keeps a ring of memory+1 vector slots for its
+// (s, y) pairs, so a new pair can be formed and tested before the oldest one
+// is dropped.
 //
 // The vectors and every scalar the recursion needs stay on the device: the
 // two-loop recursion is one launch, and the host reads scalars only where
 // its own decisions need them -- g.d after the recursion (descent test and
 // line-search start), the cost and phi'(stp) after each trial evaluation,
-// and s.y, y.y and |g| once per iteration (pair test, convergence test).
+// and s.y, y.y and |g| once per round (pair test, convergence test).
+// da_assimilate is: start every member, rounds until all have finished.
 // ---------------------------------------------------------------------------
 
 namespace {
 
 constexpr int kMaxMemory = 64;  // pairs; the recursion keeps its alphas in shared memory
 
+enum Phase { IDLE = 0, STARTED = 1, ITERATING = 2, FINISHED = 3 };
+
 struct Member {
+  int phase = IDLE;
+  int state = 0;            // 0 running, 1 converged, 2 line-search failure, 3 diverged
+  int max_iter = 0;
+  int k = 0;                // iterations begun
+  int iters = 0;            // iterations that accepted a step
+  int pending = -1;         // slot of a pair accepted in this round, tested at its end
+  double c1 = 1e-4, c2 = 0.9, gtol = 1e-10;
+  int max_ls = 20;
   std::vector<int> pairs;   // slot indices, oldest first (at most `memory`)
   std::vector<double> rho;  // 1 / (s . y) per pair
   double f = 0, gnorm = 0, g0norm = 0;
-  int state = 0;            // 0 active, 1 converged, 2 line-search failure, 3 diverged
-  int iters = 0;
-  int pending = -1;         // slot of a pair accepted in this iteration, tested at its end
+  std::vector<double> hist;  // the cost at the start and after each accepted iteration
 };
+
+struct OptState {
+  int m = 0;  // memory (pairs), fixed per context
+  std::vector<Member> mb;
+};
+
+OptState& state_of(da_ctx* c) { return *static_cast<OptState*>(c->lb_state); }
 
 // Per-call argument tables of the vector kernels, staged on the host and
 // copied to the context's argument buffers (pageable host memory: the copy
@@ -43,8 +67,8 @@ struct Args {
   da_ctx* c;
   cudaStream_t st;
   int B, m;
-  std::vector<int> ints;        // mask [B], cnt [B], aslot [B], pslot [B][m]
-  std::vector<double> dbls;     // stp [B], prho [B][m]
+  std::vector<int> ints;     // mask [B], cnt [B], aslot [B], pslot [B][m]
+  std::vector<double> dbls;  // stp [B], prho [B][m]
 
   Args(da_ctx* c_, cudaStream_t s, int B_, int m_) : c(c_), st(s), B(B_), m(m_) {
     ints.assign((size_t)3 * B + (size_t)B * m, 0);
@@ -93,6 +117,8 @@ da_status read_scalars(da_ctx* c, cudaStream_t st) {
 }
 
 da_status alloc_optimiser(da_ctx* c, int m) {
+  if (c->mem == m) return DA_OK;
+  if (c->mem) return fail(c, DA_EINVAL, "memory must stay the same across calls on one context");
   const size_t B = c->B, len = (size_t)c->n * c->n, slots = m + 1;
   da_status r = DA_OK;
   auto A = [&](da_status x) {
@@ -110,18 +136,15 @@ da_status alloc_optimiser(da_ctx* c, int m) {
     return fail(c, DA_ENOMEM, "pinned host buffer of the optimiser");
   }
   c->lb_host = static_cast<double*>(h);
+  auto* S = new OptState();
+  S->m = m;
+  S->mb.resize(c->B);
+  c->lb_state = S;
   c->mem = m;
   return DA_OK;
 }
 
-}  // namespace
-
-extern "C" da_status da_assimilate(da_ctx* c, double* s, int max_iter, const da_lbfgs_opts* opts, double* J_hist,
-                                   int* iters_done, int* member_status, void* stream) {
-  if (!c || !s || !J_hist || !iters_done || max_iter < 0) return fail(c, DA_EINVAL, "bad arguments");
-  if (!c->have_obs) return fail(c, DA_EINVAL, "no observations: call da_set_observations first");
-  if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
-  cudaStream_t st = (cudaStream_t)stream;
+da_lbfgs_opts resolve(const da_lbfgs_opts* opts) {
   da_lbfgs_opts o{10, 1e-4, 0.9, 1e-10, 20};
   if (opts) {
     if (opts->memory > 0) o.memory = opts->memory;
@@ -130,51 +153,82 @@ extern "C" da_status da_assimilate(da_ctx* c, double* s, int max_iter, const da_
     if (opts->gtol_rel > 0) o.gtol_rel = opts->gtol_rel;
     if (opts->max_ls_evals > 0) o.max_ls_evals = opts->max_ls_evals;
   }
+  return o;
+}
+
+// Common checks of the calls that evaluate; allocates the optimiser.
+da_status prepare(da_ctx* c, const da_lbfgs_opts& o) {
+  if (!c->have_obs) return fail(c, DA_EINVAL, "no observations: call da_set_observations first");
+  if (!c->dev.traj) return fail(c, DA_EINVAL, "context was created forward-only (ckpt_every < 0)");
   if (o.memory > kMaxMemory) return fail(c, DA_EINVAL, "memory must be at most 64 pairs");
-  const int B = c->B, m = o.memory, slots = m + 1;
+  return alloc_optimiser(c, o.memory);
+}
+
+void start_member(Member& M, int max_iter, const da_lbfgs_opts& o) {
+  M = Member();
+  M.phase = STARTED;
+  M.max_iter = max_iter;
+  M.c1 = o.c1;
+  M.c2 = o.c2;
+  M.gtol = o.gtol_rel;
+  M.max_ls = o.max_ls_evals;
+}
+
+// One round: one iteration of every iterating member, the first evaluation
+// of every started one.
+da_status lbfgs_round(da_ctx* c, cudaStream_t st) {
+  OptState& S = state_of(c);
+  const int B = c->B, m = S.m, slots = m + 1;
   const size_t len = (size_t)c->n * c->n;
-  da_status r = DA_OK;
-  if (c->mem != m) {
-    if (c->mem) return fail(c, DA_EINVAL, "memory must stay the same across calls on one context");
-    if ((r = alloc_optimiser(c, m))) return r;
+  std::vector<Member>& mb = S.mb;
+  for (Member& M : mb) {  // convergence and iteration budget, at the start of an iteration
+    if (M.phase != ITERATING) continue;
+    if (M.state == 0 && M.gnorm <= M.gtol * M.g0norm) M.state = 1;
+    if (M.state != 0 || M.k >= M.max_iter) M.phase = FINISHED;
   }
+  std::vector<char> active(B, 0), fresh(B, 0);
+  bool any_active = false, any_fresh = false;
+  for (int b = 0; b < B; ++b) {
+    active[b] = mb[b].phase == ITERATING;
+    fresh[b] = mb[b].phase == STARTED;
+    any_active |= active[b] != 0;
+    any_fresh |= fresh[b] != 0;
+  }
+  if (!any_active && !any_fresh) return DA_OK;
+
   Args A(c, st, B, m);
   const da::LbfgsArgs dv = A.dev();
-  double* X = c->lb_V + (size_t)da::BANK_X * B * len;
-  double* G = c->lb_V + (size_t)da::BANK_G * B * len;
   double* XT = c->lb_V + (size_t)da::BANK_XT * B * len;
   double* GT = c->lb_V + (size_t)da::BANK_GT * B * len;
-  const double* hs = c->lb_host;                       // [B][SC_COUNT]
-  const double* hJ = c->lb_host + (size_t)B * da::SC_COUNT;  // [B]
+  const double* hs = c->lb_host;
+  const double* hJ = c->lb_host + (size_t)B * da::SC_COUNT;
   auto sc = [&](int b, int k) { return hs[(size_t)b * da::SC_COUNT + k]; };
   const dim3 ew((unsigned)((len + 4095) / 4096), B);  // element-wise kernels: 4096 elements per CTA
-  std::vector<Member> mb(B);
+  da_status r;
 
-  DA_TRY_CUDA(c, cudaMemcpyAsync(X, s, B * len * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  if ((r = da_cost_grad(c, X, c->lb_J, G, st))) return r;
-  da::k_gnorm2<<<B, da::kBlasThreads, 0, st>>>(dv);
-  if ((r = check_launch(c))) return r;
-  if ((r = read_scalars(c, st))) return r;
-  for (int b = 0; b < B; ++b) {
-    mb[b].f = hJ[b];
-    mb[b].g0norm = mb[b].gnorm = std::sqrt(sc(b, da::SC_GG));
-    if (!std::isfinite(hJ[b]) || !std::isfinite(sc(b, da::SC_GG))) mb[b].state = 3;
-    J_hist[(size_t)b * (max_iter + 1)] = hJ[b];
-  }
+  // the first evaluation of started members: g = gt, cost J (|g| at the end)
+  auto take_fresh = [&]() -> da_status {
+    for (int b = 0; b < B; ++b) A.mask()[b] = fresh[b];
+    if ((r = A.upload())) return r;
+    da::k_take_gradient<<<ew, 256, 0, st>>>(dv);
+    return check_launch(c);
+  };
+  auto record_fresh = [&]() {
+    for (int b = 0; b < B; ++b)
+      if (fresh[b]) {
+        mb[b].f = hJ[b];
+        mb[b].hist.assign(1, hJ[b]);
+      }
+  };
 
-  for (int it = 0; it < max_iter; ++it) {
-    bool any = false;
+  std::vector<double> gd(B, 0.0);
+  std::vector<da::MoreThuente> ls(B);
+  std::vector<char> searching(B, 0);
+  if (any_active) {
+    // d = -H g by the two-loop recursion, one launch for every iterating member
     for (int b = 0; b < B; ++b) {
-      if (mb[b].state == 0 && mb[b].gnorm <= o.gtol_rel * mb[b].g0norm) mb[b].state = 1;
-      any |= mb[b].state == 0;
-    }
-    if (!any) break;
-    auto active = [&](int b) { return mb[b].state == 0; };
-
-    // d = -H g by the two-loop recursion, one launch for every active member
-    for (int b = 0; b < B; ++b) {
-      A.mask()[b] = active(b);
-      const int cnt = active(b) ? (int)mb[b].pairs.size() : 0;
+      A.mask()[b] = active[b];
+      const int cnt = active[b] ? (int)mb[b].pairs.size() : 0;
       A.cnt()[b] = cnt;
       for (int j = 0; j < cnt; ++j) {
         A.pslot()[(size_t)b * m + j] = mb[b].pairs[j];
@@ -185,11 +239,10 @@ extern "C" da_status da_assimilate(da_ctx* c, double* s, int max_iter, const da_
     da::k_two_loop<<<B, da::kBlasThreads, 0, st>>>(dv);
     if ((r = check_launch(c))) return r;
     if ((r = read_scalars(c, st))) return r;
-    std::vector<double> gd(B, 0.0);
     bool reset = false;
     for (int b = 0; b < B; ++b) {
       A.mask()[b] = 0;
-      if (!active(b)) continue;
+      if (!active[b]) continue;
       gd[b] = sc(b, da::SC_GD);
       if (!(gd[b] < 0.0)) {  // not a descent direction: restart from -g
         mb[b].pairs.clear();
@@ -204,97 +257,207 @@ extern "C" da_status da_assimilate(da_ctx* c, double* s, int max_iter, const da_
       da::k_neg_grad<<<ew, 256, 0, st>>>(dv);
       if ((r = check_launch(c))) return r;
     }
-
-    // line search, all searching members together
-    std::vector<da::MoreThuente> ls(B);
-    std::vector<int> searching(B, 0);
     for (int b = 0; b < B; ++b) {
-      if (!active(b)) continue;
-      const double s0 = it == 0 ? std::min(1.0, 1.0 / mb[b].gnorm) : 1.0;
-      ls[b].start(mb[b].f, gd[b], s0, o.c1, o.c2, 1e-10, 1e-20, 1e20, o.max_ls_evals);
+      if (!active[b]) continue;
+      Member& M = mb[b];
+      const double s0 = M.k == 0 ? std::min(1.0, 1.0 / M.gnorm) : 1.0;
+      ls[b].start(M.f, gd[b], s0, M.c1, M.c2, 1e-10, 1e-20, 1e20, M.max_ls);
       searching[b] = 1;
+      ++M.k;
     }
-    for (;;) {
-      bool anys = false;
-      for (int b = 0; b < B; ++b) anys |= searching[b] != 0;
-      if (!anys) break;
-      // xt = x + stp d for searching members, x otherwise
-      for (int b = 0; b < B; ++b) {
-        A.mask()[b] = searching[b];
-        A.stp()[b] = searching[b] ? ls[b].stp() : 0.0;
-      }
-      if ((r = A.upload())) return r;
-      da::k_trial<<<ew, 256, 0, st>>>(dv);
-      if ((r = check_launch(c))) return r;
-      if ((r = da_cost_grad(c, XT, c->lb_J, GT, st))) return r;
-      da::k_dot_gt_d<<<B, da::kBlasThreads, 0, st>>>(dv);
-      if ((r = check_launch(c))) return r;
-      if ((r = read_scalars(c, st))) return r;
-      bool accept_any = false;
-      for (int b = 0; b < B; ++b) A.mask()[b] = 0;
-      for (int b = 0; b < B; ++b) {
-        if (!searching[b]) continue;
-        const double ft = hJ[b], dg = sc(b, da::SC_DG);
-        if (!std::isfinite(ft) || !std::isfinite(dg)) {
-          searching[b] = 0;
-          mb[b].state = 3;
-          continue;
-        }
-        const int act = ls[b].step(ft, dg);
-        if (act == da::MoreThuente::EVALUATE) continue;
-        searching[b] = 0;
-        const bool ok = act == da::MoreThuente::CONVERGED;
-        if (ok || ft < mb[b].f) {
-          // accept: the new pair goes to a free slot, s = xt - x, y = gt - g
-          int freeslot = 0;
-          for (int t = 0; t < slots; ++t)
-            if (std::find(mb[b].pairs.begin(), mb[b].pairs.end(), t) == mb[b].pairs.end()) {
-              freeslot = t;
-              break;
-            }
-          mb[b].pending = freeslot;
-          A.mask()[b] = 1;
-          A.aslot()[b] = freeslot;
-          accept_any = true;
-          mb[b].f = ft;
-          mb[b].iters = it + 1;
-          J_hist[(size_t)b * (max_iter + 1) + it + 1] = ft;
-        }
-        if (!ok) mb[b].state = 2;
-      }
-      if (accept_any) {
-        if ((r = A.upload())) return r;
-        da::k_accept<<<B, da::kBlasThreads, 0, st>>>(dv);
-        if ((r = check_launch(c))) return r;
-      }
-    }
-    // end of the iteration: pair tests and gradient norms
-    da::k_gnorm2<<<B, da::kBlasThreads, 0, st>>>(dv);
-    if ((r = check_launch(c))) return r;
-    if ((r = read_scalars(c, st))) return r;
+  }
+  // line search, all searching members together; the first evaluation also
+  // serves the started members
+  bool first = true;
+  for (;;) {
+    bool anys = false;
+    for (int b = 0; b < B; ++b) anys |= searching[b] != 0;
+    if (!anys && !(first && any_fresh)) break;
+    std::vector<char> live(B, 0);
     for (int b = 0; b < B; ++b) {
-      if (mb[b].pending >= 0) {
-        const double sy = sc(b, da::SC_SY), yy = sc(b, da::SC_YY);
-        if (sy > 1e-16 * yy) {
-          if ((int)mb[b].pairs.size() == m) {
-            mb[b].pairs.erase(mb[b].pairs.begin());
-            mb[b].rho.erase(mb[b].rho.begin());
-          }
-          mb[b].pairs.push_back(mb[b].pending);
-          mb[b].rho.push_back(1.0 / sy);
-        }
-        mb[b].pending = -1;
-      }
-      mb[b].gnorm = std::sqrt(sc(b, da::SC_GG));
+      live[b] = searching[b] || (first && fresh[b]);
+      A.mask()[b] = searching[b];
+      A.stp()[b] = searching[b] ? ls[b].stp() : 0.0;
     }
+    if ((r = A.upload())) return r;
+    da::k_trial<<<ew, 256, 0, st>>>(dv);  // xt = x + stp d for searching members, x otherwise
+    if ((r = check_launch(c))) return r;
+    if ((r = cost_grad_members(c, XT, c->lb_J, GT, &live, st))) return r;
+    da::k_dot_gt_d<<<B, da::kBlasThreads, 0, st>>>(dv);
+    if ((r = check_launch(c))) return r;
+    if (first && any_fresh && (r = take_fresh())) return r;
+    if ((r = read_scalars(c, st))) return r;
+    if (first && any_fresh) record_fresh();
+    first = false;
+    bool accept_any = false;
+    for (int b = 0; b < B; ++b) A.mask()[b] = 0;
+    for (int b = 0; b < B; ++b) {
+      if (!searching[b]) continue;
+      Member& M = mb[b];
+      const double ft = hJ[b], dg = sc(b, da::SC_DG);
+      if (!std::isfinite(ft) || !std::isfinite(dg)) {
+        searching[b] = 0;
+        M.state = 3;
+        continue;
+      }
+      const int act = ls[b].step(ft, dg);
+      if (act == da::MoreThuente::EVALUATE) continue;
+      searching[b] = 0;
+      const bool ok = act == da::MoreThuente::CONVERGED;
+      if (ok || ft < M.f) {
+        // accept: the new pair goes to a free slot, s = xt - x, y = gt - g
+        int freeslot = 0;
+        for (int t = 0; t < slots; ++t)
+          if (std::find(M.pairs.begin(), M.pairs.end(), t) == M.pairs.end()) {
+            freeslot = t;
+            break;
+          }
+        M.pending = freeslot;
+        A.mask()[b] = 1;
+        A.aslot()[b] = freeslot;
+        accept_any = true;
+        M.f = ft;
+        M.iters = M.k;
+        M.hist.push_back(ft);
+      }
+      if (!ok) M.state = 2;
+    }
+    if (accept_any) {
+      if ((r = A.upload())) return r;
+      da::k_accept<<<B, da::kBlasThreads, 0, st>>>(dv);
+      if ((r = check_launch(c))) return r;
+    }
+  }
+  // end of the round: pair tests and gradient norms
+  da::k_gnorm2<<<B, da::kBlasThreads, 0, st>>>(dv);
+  if ((r = check_launch(c))) return r;
+  if ((r = read_scalars(c, st))) return r;
+  for (int b = 0; b < B; ++b) {
+    Member& M = mb[b];
+    if (M.pending >= 0) {
+      const double sy = sc(b, da::SC_SY), yy = sc(b, da::SC_YY);
+      if (sy > 1e-16 * yy) {
+        if ((int)M.pairs.size() == m) {
+          M.pairs.erase(M.pairs.begin());
+          M.rho.erase(M.rho.begin());
+        }
+        M.pairs.push_back(M.pending);
+        M.rho.push_back(1.0 / sy);
+      }
+      M.pending = -1;
+    }
+    if (active[b] || fresh[b]) M.gnorm = std::sqrt(sc(b, da::SC_GG));
+    if (fresh[b]) {
+      M.g0norm = M.gnorm;
+      M.phase = ITERATING;
+      if (!std::isfinite(M.f) || !std::isfinite(M.gnorm)) {
+        M.state = 3;
+        M.phase = FINISHED;
+      }
+    }
+    if (active[b] && M.state != 0) M.phase = FINISHED;
+  }
+  return DA_OK;
+}
+
+da_status member_status(const Member& M) {
+  return M.state == 3 ? DA_EDIVERGED : M.state == 2 ? DA_ENOTCONV : DA_OK;
+}
+
+}  // namespace
+
+void free_optimiser(da_ctx* c) {
+  delete static_cast<OptState*>(c->lb_state);
+  c->lb_state = nullptr;
+}
+
+extern "C" da_status da_lbfgs_start(da_ctx* c, int member, const double* s0, int max_iter,
+                                    const da_lbfgs_opts* opts, void* stream) {
+  if (!c || !s0 || max_iter < 0) return fail(c, DA_EINVAL, "bad arguments");
+  if (member < 0 || member >= c->B) return fail(c, DA_EINVAL, "member out of range");
+  const da_lbfgs_opts o = resolve(opts);
+  da_status r = prepare(c, o);
+  if (r) return r;
+  const size_t len = (size_t)c->n * c->n;
+  double* X = c->lb_V + ((size_t)da::BANK_X * c->B + member) * len;
+  DA_TRY_CUDA(c, cudaMemcpyAsync(X, s0, len * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  start_member(state_of(c).mb[member], max_iter, o);
+  return DA_OK;
+}
+
+extern "C" da_status da_lbfgs_iterate(da_ctx* c, int* running, void* stream) {
+  if (!c) return fail(c, DA_EINVAL, "ctx must not be NULL");
+  if (!c->lb_state) {
+    if (running) *running = 0;
+    return DA_OK;
+  }
+  da_status r = lbfgs_round(c, (cudaStream_t)stream);
+  if (r) return r;
+  if (running) {
+    int n = 0;
+    for (const Member& M : state_of(c).mb) n += M.phase == STARTED || M.phase == ITERATING;
+    *running = n;
+  }
+  return DA_OK;
+}
+
+extern "C" da_status da_lbfgs_member(da_ctx* c, int member, da_lbfgs_report* out, double* J_hist, int hist_len,
+                                     double* s, void* stream) {
+  if (!c || !out) return fail(c, DA_EINVAL, "ctx and out must not be NULL");
+  if (member < 0 || member >= c->B) return fail(c, DA_EINVAL, "member out of range");
+  *out = da_lbfgs_report{};
+  if (!c->lb_state) return DA_OK;
+  const Member& M = state_of(c).mb[member];
+  out->phase = M.phase;
+  out->status = member_status(M);
+  out->iters = M.iters;
+  out->J0 = M.hist.empty() ? 0.0 : M.hist.front();
+  out->J = M.f;
+  if (J_hist)
+    for (int i = 0; i < hist_len; ++i) J_hist[i] = i < (int)M.hist.size() ? M.hist[i] : M.f;
+  if (s) {
+    const size_t len = (size_t)c->n * c->n;
+    const double* X = c->lb_V + ((size_t)da::BANK_X * c->B + member) * len;
+    DA_TRY_CUDA(c, cudaMemcpyAsync(s, X, len * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  }
+  return DA_OK;
+}
+
+extern "C" da_status da_lbfgs_release(da_ctx* c, int member) {
+  if (!c) return fail(c, DA_EINVAL, "ctx must not be NULL");
+  if (member < 0 || member >= c->B) return fail(c, DA_EINVAL, "member out of range");
+  if (c->lb_state) state_of(c).mb[member] = Member();
+  return DA_OK;
+}
+
+extern "C" da_status da_assimilate(da_ctx* c, double* s, int max_iter, const da_lbfgs_opts* opts, double* J_hist,
+                                   int* iters_done, int* member_status_out, void* stream) {
+  if (!c || !s || !J_hist || !iters_done || max_iter < 0) return fail(c, DA_EINVAL, "bad arguments");
+  const da_lbfgs_opts o = resolve(opts);
+  da_status r = prepare(c, o);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int B = c->B;
+  const size_t len = (size_t)c->n * c->n;
+  double* X = c->lb_V + (size_t)da::BANK_X * B * len;
+  DA_TRY_CUDA(c, cudaMemcpyAsync(X, s, B * len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  OptState& S = state_of(c);
+  for (int b = 0; b < B; ++b) start_member(S.mb[b], max_iter, o);
+  for (;;) {
+    bool running = false;
+    for (const Member& M : S.mb) running |= M.phase == STARTED || M.phase == ITERATING;
+    if (!running) break;
+    if ((r = lbfgs_round(c, st))) return r;
   }
   bool diverged = false, failed = false;
   std::string who;
   for (int b = 0; b < B; ++b) {
-    iters_done[b] = mb[b].iters;
-    for (int it = mb[b].iters + 1; it <= max_iter; ++it) J_hist[(size_t)b * (max_iter + 1) + it] = mb[b].f;
-    const da_status ms = mb[b].state == 3 ? DA_EDIVERGED : mb[b].state == 2 ? DA_ENOTCONV : DA_OK;
-    if (member_status) member_status[b] = ms;
+    const Member& M = S.mb[b];
+    iters_done[b] = M.iters;
+    for (int it = 0; it <= max_iter; ++it)
+      J_hist[(size_t)b * (max_iter + 1) + it] = it < (int)M.hist.size() ? M.hist[it] : M.f;
+    const da_status ms = member_status(M);
+    if (member_status_out) member_status_out[b] = ms;
     diverged |= ms == DA_EDIVERGED;
     failed |= ms == DA_ENOTCONV;
     if (ms != DA_OK) who += (who.empty() ? "" : ", ") + std::to_string(b);

@@ -21,12 +21,12 @@ struct Ops {
   void (*half_to_compact)(const Dev&, const double2* in, double2* dst, cudaStream_t);
   void (*ctrl_cols)(const Dev&, int flags, cudaStream_t);
   void (*fwd_rows)(const Dev&, int n, int stage, int flags, cudaStream_t);
-  void (*fwd_cols)(const Dev&, int stage, int flags, cudaStream_t);
+  void (*fwd_cols)(const Dev&, int n, int stage, int flags, cudaStream_t);
   void (*state_cols)(const Dev&, cudaStream_t);
   void (*adj_init)(const Dev&, int mode, cudaStream_t);
   void (*adj_rows)(const Dev&, int n, int stage, cudaStream_t);
   void (*adj_cols)(const Dev&, int n, int stage, int flags, cudaStream_t);
-  void (*make_mult)(const Dev&, double* mult, const int* kind, const double* param, const double* table, double nu,
+  void (*make_mult)(const Dev&, double* mult, const int* kind, const double* param, const double* table, const double* nu,
                     cudaStream_t);
 };
 

@@ -55,8 +55,8 @@ Ops make_ops() {
   o.fwd_rows = [](const Dev& d, int n, int stage, int flags, cudaStream_t st) {
     k_fwd_rows<N, V><<<dim3(N / 2, d.B), G::THREADS, G::SMEM, st>>>(d, n, stage, flags);
   };
-  o.fwd_cols = [](const Dev& d, int stage, int flags, cudaStream_t st) {
-    k_fwd_cols<N, V><<<dim3(G::Kc, d.B), G::THREADS, G::SMEM, st>>>(d, stage, flags);
+  o.fwd_cols = [](const Dev& d, int n, int stage, int flags, cudaStream_t st) {
+    k_fwd_cols<N, V><<<dim3(G::Kc, d.B), G::THREADS, G::SMEM, st>>>(d, n, stage, flags);
   };
   o.state_cols = [](const Dev& d, cudaStream_t st) {
     k_state_cols<N, V><<<dim3(G::Kc, d.B), G::THREADS, G::SMEM, st>>>(d);
@@ -70,7 +70,7 @@ Ops make_ops() {
   o.adj_cols = [](const Dev& d, int n, int stage, int flags, cudaStream_t st) {
     k_adj_cols<N, V><<<dim3(G::Kc, d.B), G::THREADS, G::SMEM, st>>>(d, n, stage, flags);
   };
-  o.make_mult = [](const Dev& d, double* mult, const int* kind, const double* param, const double* table, double nu,
+  o.make_mult = [](const Dev& d, double* mult, const int* kind, const double* param, const double* table, const double* nu,
                    cudaStream_t st) {
     k_make_mult<N, V><<<dim3((G::Kr * G::Kc + 255) / 256, d.B), 256, 0, st>>>(mult, kind, param, table, nu);
   };

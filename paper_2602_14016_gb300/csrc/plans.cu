@@ -29,9 +29,11 @@ static da_status set_plan(da_ctx* c, int v) {
   DA_TRY_CUDA(c, cudaMemcpy((void*)c->dev.fold, fold.data(), fold.size() * sizeof(double), cudaMemcpyHostToDevice));
   DA_TRY_CUDA(c, o->setup());
   c->ops = o;
-  if (c->cg_exec) {
-    cudaGraphExecDestroy(c->cg_exec);
-    c->cg_exec = nullptr;
+  drop_graphs(c);
+  if (c->sp_exec) {
+    cudaGraphExecDestroy(c->sp_exec);
+    c->sp_exec = nullptr;
+    c->sp_key = -1;
   }
   c->have_fwd = false;
   return DA_OK;
@@ -64,14 +66,15 @@ static da_status clear_state(da_ctx* c, cudaStream_t st) {
 // context stores stage fields) over whatever the working buffers hold.
 static da_status tuning_steps(da_ctx* c, int steps, cudaStream_t st) {
   const Ops* o = c->ops;
-  Dev& d = c->dev;
+  c->dev.seg0 = 0;
+  Dev d = c->dev;
+  d.ragged = 0;  // every member works, whatever windows a ragged batch holds
   const bool store = d.traj != nullptr;
-  d.seg0 = 0;
   for (int i = 0; i < steps; ++i) {
     const int k = store ? i % d.traj_steps : 0;
     for (int j = 1; j <= 4; ++j) {
       o->fwd_rows(d, k, j, store ? da::F_STORE : 0, st);
-      o->fwd_cols(d, j, 0, st);
+      o->fwd_cols(d, k, j, 0, st);
     }
     if (store)
       for (int j = 4; j >= 1; --j) {

@@ -7,10 +7,10 @@ namespace da {
 // order (deterministic).  grid B, block 256.
 __global__ void k_residual(Dev d) {
   const int bm = blockIdx.x;
-  const int cnt = d.nt * d.px * d.px * 2;
-  const double* o = d.obs + (size_t)bm * cnt;
-  const double* m = d.mobs + (size_t)bm * cnt;
-  double* r = d.res + (size_t)bm * cnt;
+  const int cnt = d.ragged ? d.mnt[bm] * d.mpx[bm] * d.mpx[bm] * 2 : d.nt * d.px * d.px * 2;
+  const double* o = d.obs + bm * d.obs_stride;
+  const double* m = d.mobs + bm * d.obs_stride;
+  double* r = d.res + bm * d.obs_stride;
   double acc = 0.0;
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
     const double v = o[i] - m[i];

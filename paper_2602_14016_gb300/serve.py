@@ -11,6 +11,13 @@ a job that arrives while others run starts as soon as memory and a slot
 free up, without waiting for a batch boundary.  Each job's result does not
 depend on what else runs (own context, deterministic kernels).
 
+`CoBatchServer` goes further and shares launches between jobs: per grid size
+one pool context holds a fixed number of member slots (a ragged batch, its
+memory allocated once); a job of that grid takes a free slot between two
+L-BFGS rounds of the pool and leaves it when it finishes, and every round is
+one lockstep iteration of all the pool's jobs, so their forward and adjoint
+sweeps run in the same launches (da_set_member, da_lbfgs_*).
+
 Reports per job: arrival, admission and completion times; overall:
 solves/s, p50/p99 latency.  `FakeExecutor` replaces the GPU for tests of
 the admission and accounting logic on the CPU.
@@ -70,7 +77,7 @@ def context_bytes(n: int, nsteps: int, px: int, every: int, ckpt_every: int, bat
     nt = nsteps // every
     comp = batch * Kr * Kc * 16
     b = 6 * comp + batch * 4 * n * Kc * 16 + 3 * batch * nt * px * px * 2 * 8 + comp // 2
-    b += n * 16 + px * 16 + batch * (8 + 4 + 8) + batch * 8 + Kr * Kc * 72
+    b += n * 16 + 64 * 16 + batch * (8 + 4 + 8) + batch * 8 + Kr * Kc * 72 + batch * (4 * 4 + 8)
     if ckpt_every == 0:
         b += batch * nsteps * 8 * n * n * 8
     else:
@@ -241,3 +248,132 @@ def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
     """Arrival times of a Poisson process (seeded exponential gaps)."""
     gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=count)
     return np.cumsum(gaps) - gaps[0]
+
+
+def summarize(jobs: list, **extra) -> dict:
+    """solves/s and p50/p99 latency of finished jobs (a solve returns a
+    control: converged, out of iterations, or stopped by the line search)."""
+    makespan = max(j.t_done for j in jobs) - min(j.arrival for j in jobs)
+    lat = np.array([j.latency for j in jobs])
+    solved = [j for j in jobs if j.status in (0, 6)]
+    out = {"jobs": len(jobs), "solves": len(solved), "failed": len(jobs) - len(solved),
+           "solves_per_s": len(solved) / makespan, "makespan_s": makespan,
+           "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99))}
+    out.update(extra)
+    return out
+
+
+class CoBatchServer:
+    """Continuous batching in shared launches.
+
+    pools: {n: dict(slots=S, nsteps=max horizon, px=max probes per side,
+    dt=..., ckpt_every=K)} -- one pool context per grid size, created once
+    (forcing available, members switch it on or off).  Each pool runs on its
+    own host thread and CUDA stream: between rounds it admits the arrived
+    jobs of its grid into free slots (their windows, kernels, observations and
+    first guesses), runs one round (da_lbfgs_iterate: an L-BFGS iteration of
+    every member in shared launches), and retires the members that finished.
+    Plan variant `plan` on every pool, so a job's result equals its result in
+    a batch-1 context on that variant."""
+
+    def __init__(self, pools: dict, device: int = 0, graphs: bool = True, plan: int = 0, every: int = 10):
+        import torch
+
+        from . import api
+
+        self.torch, self.api = torch, api
+        self.device = device
+        self.pools = {}
+        self.every = every
+        for n, p in pools.items():
+            cfg = api.Config(n=n, nsteps=p["nsteps"], dt=p["dt"], nu=1e-3, forcing="kolmogorov", nf=4,
+                             px=p["px"], every=every, kernels=[api.KernelSpec("identity", 0.0)] * p["slots"],
+                             ckpt_every=p.get("ckpt_every", 0))
+            with torch.cuda.device(device):
+                ctx = api.Context(cfg, device)
+                ctx.set_plan(plan)
+                if graphs:
+                    ctx.set_graphs(True)
+                for b in range(p["slots"]):
+                    ctx.set_member(b, 0)
+                self.pools[n] = {"ctx": ctx, "slots": p["slots"], "stream": torch.cuda.Stream(device),
+                                 "jobs": [None] * p["slots"], "rounds": 0}
+        self.peak_members = 0
+
+    @staticmethod
+    def pool_bytes(n: int, nsteps: int, px: int, every: int, ckpt_every: int, slots: int) -> int:
+        return context_bytes(n, nsteps, px, every, ckpt_every, batch=slots)
+
+    def _pool_loop(self, n, pool, queue, lock, t0, errors):
+        torch, api = self.torch, self.api
+        ctx, st = pool["ctx"], pool["stream"]
+        slots = pool["jobs"]
+        try:
+            with torch.cuda.device(self.device), torch.cuda.stream(st):
+                while True:
+                    now = time.perf_counter() - t0
+                    with lock:
+                        arrived = [j for j in queue if j.arrival <= now]
+                        for j in arrived:
+                            if None not in slots:
+                                break
+                            b = slots.index(None)
+                            queue.remove(j)
+                            slots[b] = j
+                            j.t_admit = now
+                            kern = api.KernelSpec(*j.kernel)
+                            ctx.set_member(b, j.nsteps, j.px, j.nu, j.forcing == "kolmogorov", kern,
+                                           torch.from_numpy(j.m[0]), stream=st)
+                            ctx.lbfgs_start(b, torch.from_numpy(j.s0[0]).to(ctx.device), j.iters, stream=st)
+                        busy = sum(x is not None for x in slots)
+                        self.peak_members = max(self.peak_members, busy)
+                        remaining = len(queue)
+                    if busy == 0:
+                        if remaining == 0:
+                            return
+                        nxt = min(j.arrival for j in queue)
+                        time.sleep(max(0.0, min(0.05, nxt - (time.perf_counter() - t0))))
+                        continue
+                    ctx.lbfgs_iterate(stream=st)
+                    pool["rounds"] += 1
+                    for b, j in enumerate(slots):
+                        if j is None:
+                            continue
+                        rep, hist, s = ctx.lbfgs_member(b, j.iters + 1, control=True, stream=st)
+                        if rep["phase"] != 3:
+                            continue
+                        st.synchronize()
+                        j.J_hist, j.iters_done, j.status = hist, rep["iters"], rep["status"]
+                        j.s = s.cpu().numpy()[None]
+                        j.t_done = time.perf_counter() - t0
+                        ctx.lbfgs_release(b)
+                        ctx.set_member(b, 0, stream=st)
+                        slots[b] = None
+        except Exception as e:  # recorded; the run reports it
+            errors.append((n, repr(e)))
+
+    def run(self, jobs: list) -> dict:
+        for j in jobs:
+            if j.n not in self.pools:
+                raise ValueError(f"job {j.job_id}: no pool for grid {j.n}")
+            if j.every != self.every:
+                raise ValueError(f"job {j.job_id}: observation interval {j.every} != the pools' {self.every}")
+        lock = threading.Lock()
+        t0 = time.perf_counter()
+        errors = []
+        threads = []
+        for n, pool in self.pools.items():
+            queue = sorted([j for j in jobs if j.n == n], key=lambda j: j.arrival)
+            th = threading.Thread(target=self._pool_loop, args=(n, pool, queue, lock, t0, errors), daemon=True)
+            th.start()
+            threads.append(th)
+        for th in threads:
+            th.join()
+        if errors:
+            raise RuntimeError(f"pool failures: {errors}")
+        return summarize(jobs, peak_members=self.peak_members,
+                         rounds={int(n): p["rounds"] for n, p in self.pools.items()})
+
+    def close(self):
+        for p in self.pools.values():
+            p["ctx"].close()

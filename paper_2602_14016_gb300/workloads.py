@@ -74,6 +74,7 @@ def ensemble_statistics(api, torch, groups, nsteps=1000, save_every=10, ckpt_eve
                          kernels=[api.KernelSpec("identity", 0.0)] * B, ckpt_every=ckpt_every)
         ctx = api.Context(cfg)
         g["fft_plan"], g["plan_ms_per_step"] = ctx.autotune(4)  # the autotuner picks the plan per grid and batch
+        ctx.set_graphs(True)  # the whole sweep (forward, recompute, adjoint, spectra) as one CUDA graph
         w = torch.from_numpy(np.stack([synthetic.random_vorticity_hat(n, g["seed0"] + b) for b in range(B)]))
         s = ctx.control_from_omega(w.to(ctx.device))
         lamT = torch.from_numpy(np.stack([synthetic.unit_norm_terminal_hat(n, 10_000 + g["seed0"] + b)

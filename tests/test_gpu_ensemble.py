@@ -71,3 +71,26 @@ def test_adjoint_spectra_against_oracle(orc, api, ckpt):
     ux = np.fft.irfft2(1j * KY * lam, s=(n, n))
     uy = np.fft.irfft2(-1j * KX * lam, s=(n, n))
     assert abs(member[0, 0].sum() - 0.5 * np.mean(ux**2 + uy**2)) < 1e-12 * member[0, 0].sum()
+
+
+@pytest.mark.parametrize("ckpt", [0, 4])
+def test_graph_replayed_spectra_equal_direct_launches(api, ckpt):
+    """da_adjoint_spectra under da_set_graphs: the captured sequence, replayed
+    twice (the second time on new inputs), gives bitwise the direct launches'
+    spectra and gradient state."""
+    n, B, nsteps = 32, 3, 12
+    cfg = api.Config(n=n, nsteps=nsteps, dt=5e-3, nu=1e-3, px=1, every=nsteps, ckpt_every=ckpt,
+                     kernels=[api.KernelSpec("identity", 0.0)] * B)
+    direct, graph = api.Context(cfg), api.Context(cfg)
+    graph.set_graphs(True)
+    for rep in range(2):
+        w = torch.from_numpy(np.stack([synthetic.random_vorticity_hat(n, 50 * rep + b) for b in range(B)])).cuda()
+        s = direct.control_from_omega(w)
+        lamT = torch.from_numpy(np.stack([synthetic.unit_norm_terminal_hat(n, 90 + 50 * rep + b)
+                                          for b in range(B)])).cuda()
+        m1, e1 = direct.adjoint_spectra(s, lamT, 3)
+        m2, e2 = graph.adjoint_spectra(s, lamT, 3)
+        l1, _ = direct.last_adjoint()
+        l2, _ = graph.last_adjoint()
+        torch.cuda.synchronize()
+        assert torch.equal(m1, m2) and torch.equal(e1, e2) and torch.equal(l1, l2)

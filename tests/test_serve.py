@@ -104,3 +104,41 @@ def test_results_are_the_same_alone_and_in_the_mix():
         assert j.iters_done == a.iters_done
         assert np.array_equal(j.J_hist, a.J_hist)
         assert np.array_equal(j.s, a.s)
+
+
+@pytest.mark.gpu
+def test_co_batched_results_equal_the_alone_results():
+    """Jobs of two grid sizes through the co-batching server (pool slots,
+    admission between L-BFGS rounds, shared launches) end with bitwise the
+    histories and controls of the same jobs run one at a time."""
+    torch = pytest.importorskip("torch")
+    import oracle
+    from paper_2602_14016_gb300 import synthetic
+
+    specs = [(32, 20, ("exp_abs", 0.5), "none", 1e-3), (32, 40, ("frac", 1.0), "kolmogorov", 1e-2),
+             (64, 20, ("frac", 0.5), "none", 1e-3), (32, 10, ("identity", 0.0), "kolmogorov", 1e-2),
+             (64, 10, ("exp_sq", 0.7), "kolmogorov", 1e-2)]
+    jobs = []
+    for i, (n, nsteps, kern, flow, nu) in enumerate(specs):
+        px = 8 if i % 2 == 0 else 4
+        P = oracle.Problem(n=n, nsteps=nsteps, dt=5e-3, nu=nu, forcing=flow, nf=4, px=px, every=5, kernel=kern[0],
+                           kparam=kern[1])
+        truth = oracle.control_from_omega(P, synthetic.random_vorticity_hat(n, 600 + i) * 2)
+        guess = oracle.control_from_omega(P, synthetic.random_vorticity_hat(n, 700 + i) * 2)
+        _, m = oracle.forward(P, truth)
+        jobs.append(serve.Job(job_id=i, n=n, nsteps=nsteps, dt=5e-3, nu=nu, px=px, every=5, kernel=kern,
+                              forcing=flow, nf=4, iters=4, arrival=0.02 * i, m=m[None].copy(), s0=guess[None].copy()))
+    alone = []
+    for j in jobs:
+        a = serve.Job(**{f.name: getattr(j, f.name) for f in serve.dataclasses.fields(serve.Job)})
+        serve.Server(serve.CudaExecutor(), memory_budget=1 << 36, slots=1).run([a])
+        alone.append(a)
+    srv = serve.CoBatchServer({32: dict(slots=2, nsteps=40, px=8, dt=5e-3), 64: dict(slots=2, nsteps=20, px=8,
+                                                                                      dt=5e-3)}, every=5)
+    out = srv.run(jobs)
+    srv.close()
+    assert out["jobs"] == len(jobs) and out["failed"] == 0 and out["peak_members"] >= 2
+    for a, j in zip(alone, jobs):
+        assert j.status == a.status and j.iters_done == a.iters_done, (j.job_id, j.status, a.status)
+        assert np.array_equal(j.J_hist, a.J_hist), (j.job_id, j.J_hist, a.J_hist)
+        assert np.array_equal(j.s, a.s), j.job_id
