@@ -569,11 +569,11 @@ def run_workload(args):
                 share = budget // len(args.serve_grids)
                 nmax = args.serve_steps[1] // 10 * 10
                 ck = 0
-                if serve.CoBatchServer.pool_bytes(n, nmax, 32, 10, 0, args.slots) > share:
+                if serve.CoBatchServer.pool_bytes(n, nmax, 32, 10, 0, args.co_slots) > share:
                     ck = next((K for K in range(nmax, 0, -1)
-                               if serve.CoBatchServer.pool_bytes(n, nmax, 32, 10, K, args.slots) <= share), 1)
-                pools[n] = dict(slots=args.slots, nsteps=nmax, px=32, dt=dts[n], ckpt_every=ck)
-            co = serve.CoBatchServer(pools)
+                               if serve.CoBatchServer.pool_bytes(n, nmax, 32, 10, K, args.co_slots) <= share), 1)
+                pools[n] = dict(slots=args.co_slots, nsteps=nmax, px=32, dt=dts[n], ckpt_every=ck)
+            co = serve.CoBatchServer(pools, plan=None)
             out_co = co.run(fresh_jobs())
             co.close()
             torch.cuda.empty_cache()
@@ -584,7 +584,8 @@ def run_workload(args):
             summary[str(rate)] = {"co_batched": out_co, "stream_overlap": out, "one_job_at_a_time": base,
                                   "pools": {str(n): p for n, p in pools.items()}}
         line.update({"metric": "served solves/s, p50/p99 latency", "rates": summary,
-                     "config": {"jobs": args.serve_jobs, "slots": args.slots, "grids": args.serve_grids,
+                     "config": {"jobs": args.serve_jobs, "slots": args.slots, "co_slots": args.co_slots,
+                                "grids": args.serve_grids,
                                 "grid_weights": args.serve_weights, "horizon_steps": args.serve_steps,
                                 "lbfgs_iters": args.serve_iters}})
     print(json.dumps(line), flush=True)
@@ -616,6 +617,7 @@ def main():
     ap.add_argument("--rates", type=float, nargs="+", default=[2.0, 10.0])
     ap.add_argument("--serve-jobs", type=int, default=16)
     ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--co-slots", type=int, default=8, help="member slots per grid-size pool of the co-batched server")
     # job mix; the defaults are a scaled-down mix that a run finishes in
     # minutes, the full one is --serve-grids 128 256 512 1024
     # --serve-weights 0.4 0.3 0.2 0.1 --serve-steps 500 4000 --serve-iters 30

@@ -274,9 +274,11 @@ class CoBatchServer:
     first guesses), runs one round (da_lbfgs_iterate: an L-BFGS iteration of
     every member in shared launches), and retires the members that finished.
     Plan variant `plan` on every pool, so a job's result equals its result in
-    a batch-1 context on that variant."""
+    a batch-1 context on that variant; plan=None lets the autotuner pick each
+    pool's variant for its slot count (results then equal the batch-1 ones to
+    rounding)."""
 
-    def __init__(self, pools: dict, device: int = 0, graphs: bool = True, plan: int = 0, every: int = 10):
+    def __init__(self, pools: dict, device: int = 0, graphs: bool = True, plan: Optional[int] = 0, every: int = 10):
         import torch
 
         from . import api
@@ -291,7 +293,10 @@ class CoBatchServer:
                              ckpt_every=p.get("ckpt_every", 0))
             with torch.cuda.device(device):
                 ctx = api.Context(cfg, device)
-                ctx.set_plan(plan)
+                if plan is None:
+                    ctx.autotune(4)
+                else:
+                    ctx.set_plan(plan)
                 if graphs:
                     ctx.set_graphs(True)
                 for b in range(p["slots"]):
