@@ -52,9 +52,9 @@ def member_data(orc, b, win):
     return P, guess, noisy_observations(m, 500 + b)
 
 
-def ragged_context(api, graphs=False):
+def ragged_context(api, graphs=False, ckpt=0):
     cfg = api.Config(n=N, nsteps=NSTEPS, dt=DT, nu=1e-3, forcing="kolmogorov", nf=4, px=PMAX, every=EVERY,
-                     kernels=[api.KernelSpec("identity", 0.0)] * len(WINDOWS))
+                     kernels=[api.KernelSpec("identity", 0.0)] * len(WINDOWS), ckpt_every=ckpt)
     ctx = api.Context(cfg)
     ctx.set_plan(0)
     if graphs:
@@ -72,9 +72,11 @@ def alone_context(api, win, m):
     return ctx
 
 
-@pytest.mark.parametrize("graphs", [False, True])
-def test_ragged_members_match_the_oracle_and_their_alone_runs(orc, api, graphs):
-    ctx = ragged_context(api, graphs)
+@pytest.mark.parametrize("graphs,ckpt", [(False, 0), (True, 0), (False, 7), (True, 3)])
+def test_ragged_members_match_the_oracle_and_their_alone_runs(orc, api, graphs, ckpt):
+    """With checkpoints every 7 or 3 steps the segments cut through the
+    members' windows (starts at steps 0, 5 and 20 of the 40-step evaluation)."""
+    ctx = ragged_context(api, graphs, ckpt)
     data = {}
     s = np.zeros((len(WINDOWS), N, N))
     for b, win in enumerate(WINDOWS):
