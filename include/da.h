@@ -311,7 +311,7 @@ da_status da_set_member(da_ctx* ctx, int member, const da_member_window* w, cons
                         const double* m, void* stream);
 
 /* Stepwise L-BFGS over the member slots (Sec. II.C), for loops that start and
- * retire members between iterations: da_assimilate is da_lbfgs_start on
+ * retire members between evaluations: da_assimilate is da_lbfgs_start on
  * every member, then da_lbfgs_iterate until none runs.  A member's iterates
  * do not depend on when it started or on the other members. */
 typedef struct {
@@ -329,12 +329,17 @@ typedef struct {
 da_status da_lbfgs_start(da_ctx* ctx, int member, const double* s0, int max_iter, const da_lbfgs_opts* opts,
                          void* stream);
 
-/* One round: one L-BFGS iteration of every iterating member, in lockstep
- * (shared evaluations), and the first cost-and-gradient evaluation of every
- * member started since the last round.  A member finishes when it converges
- * (|g| <= gtol_rel |g0|), spends its budget, its line search fails or its cost
- * turns non-finite.  running (HOST, nullable): members still started or
- * iterating.  Waits for `stream` (the line search decides on the host). */
+/* One step: advances every running member to and through one shared
+ * cost-and-gradient evaluation -- members whose last trial was accepted get
+ * their (s, y) pair tested, members starting an iteration get their search
+ * direction (the two-loop recursion) and line search, and one evaluation
+ * serves every searching member's trial and every newly started member's
+ * first point.  Members at different points of their iterations share the
+ * evaluation; none waits for another's line search.  A member finishes when
+ * it converges (|g| <= gtol_rel |g0|), spends its budget, its line search
+ * fails or its cost turns non-finite.  running (HOST, nullable): members
+ * still started or iterating.  Waits for `stream` (the line search decides
+ * on the host). */
 da_status da_lbfgs_iterate(da_ctx* ctx, int* running, void* stream);
 
 /* Report of member `member` (HOST out); J_hist (HOST, nullable, hist_len

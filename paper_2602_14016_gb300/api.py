@@ -256,7 +256,7 @@ class Context:
                                             _stream(stream)))
 
     def lbfgs_iterate(self, stream=None) -> int:
-        """One lockstep round; returns the number of members still running."""
+        """One step (one shared evaluation); returns the number of members still running."""
         running = ctypes.c_int(0)
         self._check(self.lib.da_lbfgs_iterate(self.ctx, ctypes.byref(running), _stream(stream)))
         return running.value

@@ -11,24 +11,27 @@
 
 // ---------------------------------------------------------------------------
 // Every member slot of a batch has its own optimiser state.  A member is
-// started on a control (da_lbfgs_start), then each round (da_lbfgs_iterate)
-// runs one L-BFGS iteration of every iterating member in lockstep: the
-// members share every cost-gradient evaluation, and a member that is not
-// searching is left out of it (in a ragged batch its CTAs return at once) or,
-// in a homogeneous batch, re-evaluates its accepted point, which changes
-// nothing.  A member started since the last round gets its first evaluation
-// in the round's first evaluation and iterates from the next round, so the
-// arithmetic of a member does not depend on when it joined or who else is in
-// the batch.  Each member keeps a ring of memory+1 vector slots for its
-// (s, y) pairs, so a new pair can be formed and tested before the oldest one
-// is dropped.
+// started on a control (da_lbfgs_start); each step (da_lbfgs_iterate) then
+// advances every running member to and through one shared cost-gradient
+// evaluation: members whose last trial was accepted get their pair tested,
+// members that need a search direction get it (the two-loop recursion, one
+// launch for all of them) and a line search started, and one evaluation then
+// serves every searching member's trial and every newly started member's
+// first point.  Members at different points of their iterations share each
+// evaluation, and no member waits for another's line search; a member that
+// is not evaluated is left out (in a ragged batch its CTAs return at once)
+// or, in a homogeneous batch, re-evaluates its accepted point, which changes
+// nothing.  A member's own sequence of operations does not depend on when it
+// joined or who else is in the batch, so its results do not either.  Each
+// member keeps a ring of memory+1 vector slots for its (s, y) pairs, so a new
+// pair can be formed and tested before the oldest one is dropped.
 //
 // The vectors and every scalar the recursion needs stay on the device: the
 // two-loop recursion is one launch, and the host reads scalars only where
-// its own decisions need them -- g.d after the recursion (descent test and
-// line-search start), the cost and phi'(stp) after each trial evaluation,
-// and s.y, y.y and |g| once per round (pair test, convergence test).
-// da_assimilate is: start every member, rounds until all have finished.
+// its own decisions need them -- s.y, y.y and |g| after an accepted step
+// (pair and convergence tests), g.d after the recursion (descent test and
+// line-search start), and the cost and phi'(stp) after each evaluation.
+// da_assimilate is: start every member, steps until all have finished.
 // ---------------------------------------------------------------------------
 
 namespace {
@@ -36,9 +39,13 @@ namespace {
 constexpr int kMaxMemory = 64;  // pairs; the recursion keeps its alphas in shared memory
 
 enum Phase { IDLE = 0, STARTED = 1, ITERATING = 2, FINISHED = 3 };
+// where a started or iterating member is within its iteration
+enum Sub { FIRST_EVAL, FIRST_NORM, NEED_DIR, SEARCHING, ACCEPTED };
 
 struct Member {
   int phase = IDLE;
+  int sub = FIRST_EVAL;
+  da::MoreThuente ls;
   int state = 0;            // 0 running, 1 converged, 2 line-search failure, 3 diverged
   int max_iter = 0;
   int k = 0;                // iterations begun
@@ -167,6 +174,7 @@ da_status prepare(da_ctx* c, const da_lbfgs_opts& o) {
 void start_member(Member& M, int max_iter, const da_lbfgs_opts& o) {
   M = Member();
   M.phase = STARTED;
+  M.sub = FIRST_EVAL;
   M.max_iter = max_iter;
   M.c1 = o.c1;
   M.c2 = o.c2;
@@ -174,28 +182,13 @@ void start_member(Member& M, int max_iter, const da_lbfgs_opts& o) {
   M.max_ls = o.max_ls_evals;
 }
 
-// One round: one iteration of every iterating member, the first evaluation
-// of every started one.
-da_status lbfgs_round(da_ctx* c, cudaStream_t st) {
+// One step: pair tests and first norms, new directions, then one shared
+// evaluation and its results.
+da_status lbfgs_step(da_ctx* c, cudaStream_t st) {
   OptState& S = state_of(c);
   const int B = c->B, m = S.m, slots = m + 1;
   const size_t len = (size_t)c->n * c->n;
   std::vector<Member>& mb = S.mb;
-  for (Member& M : mb) {  // convergence and iteration budget, at the start of an iteration
-    if (M.phase != ITERATING) continue;
-    if (M.state == 0 && M.gnorm <= M.gtol * M.g0norm) M.state = 1;
-    if (M.state != 0 || M.k >= M.max_iter) M.phase = FINISHED;
-  }
-  std::vector<char> active(B, 0), fresh(B, 0);
-  bool any_active = false, any_fresh = false;
-  for (int b = 0; b < B; ++b) {
-    active[b] = mb[b].phase == ITERATING;
-    fresh[b] = mb[b].phase == STARTED;
-    any_active |= active[b] != 0;
-    any_fresh |= fresh[b] != 0;
-  }
-  if (!any_active && !any_fresh) return DA_OK;
-
   Args A(c, st, B, m);
   const da::LbfgsArgs dv = A.dev();
   double* XT = c->lb_V + (size_t)da::BANK_XT * B * len;
@@ -203,32 +196,65 @@ da_status lbfgs_round(da_ctx* c, cudaStream_t st) {
   const double* hs = c->lb_host;
   const double* hJ = c->lb_host + (size_t)B * da::SC_COUNT;
   auto sc = [&](int b, int k) { return hs[(size_t)b * da::SC_COUNT + k]; };
+  auto running = [&](const Member& M) { return M.phase == STARTED || M.phase == ITERATING; };
   const dim3 ew((unsigned)((len + 4095) / 4096), B);  // element-wise kernels: 4096 elements per CTA
   da_status r;
 
-  // the first evaluation of started members: g = gt, cost J (|g| at the end)
-  auto take_fresh = [&]() -> da_status {
-    for (int b = 0; b < B; ++b) A.mask()[b] = fresh[b];
-    if ((r = A.upload())) return r;
-    da::k_take_gradient<<<ew, 256, 0, st>>>(dv);
-    return check_launch(c);
-  };
-  auto record_fresh = [&]() {
-    for (int b = 0; b < B; ++b)
-      if (fresh[b]) {
-        mb[b].f = hJ[b];
-        mb[b].hist.assign(1, hJ[b]);
-      }
-  };
-
-  std::vector<double> gd(B, 0.0);
-  std::vector<da::MoreThuente> ls(B);
-  std::vector<char> searching(B, 0);
-  if (any_active) {
-    // d = -H g by the two-loop recursion, one launch for every iterating member
+  // 1. |g| after a first evaluation; the pair test and |g| after an accepted step
+  bool need_norm = false;
+  for (const Member& M : mb) need_norm |= running(M) && (M.sub == FIRST_NORM || M.sub == ACCEPTED);
+  if (need_norm) {
+    da::k_gnorm2<<<B, da::kBlasThreads, 0, st>>>(dv);
+    if ((r = check_launch(c))) return r;
+    if ((r = read_scalars(c, st))) return r;
     for (int b = 0; b < B; ++b) {
-      A.mask()[b] = active[b];
-      const int cnt = active[b] ? (int)mb[b].pairs.size() : 0;
+      Member& M = mb[b];
+      if (!running(M)) continue;
+      if (M.sub == FIRST_NORM) {
+        M.g0norm = M.gnorm = std::sqrt(sc(b, da::SC_GG));
+        M.phase = ITERATING;
+        M.sub = NEED_DIR;
+        if (!std::isfinite(M.f) || !std::isfinite(M.gnorm)) {
+          M.state = 3;
+          M.phase = FINISHED;
+        }
+      } else if (M.sub == ACCEPTED) {
+        const double sy = sc(b, da::SC_SY), yy = sc(b, da::SC_YY);
+        if (sy > 1e-16 * yy) {
+          if ((int)M.pairs.size() == m) {
+            M.pairs.erase(M.pairs.begin());
+            M.rho.erase(M.rho.begin());
+          }
+          M.pairs.push_back(M.pending);
+          M.rho.push_back(1.0 / sy);
+        }
+        M.pending = -1;
+        M.gnorm = std::sqrt(sc(b, da::SC_GG));
+        M.sub = NEED_DIR;
+        if (M.state != 0) M.phase = FINISHED;  // the line search failed after accepting a lower cost
+      }
+    }
+  }
+
+  // 2. new iterations: convergence and budget tests, then d = -H g by the
+  // two-loop recursion (one launch for all of them) and the line-search start
+  std::vector<char> dir(B, 0);
+  bool any_dir = false;
+  for (int b = 0; b < B; ++b) {
+    Member& M = mb[b];
+    if (M.phase != ITERATING || M.sub != NEED_DIR) continue;
+    if (M.state == 0 && M.gnorm <= M.gtol * M.g0norm) M.state = 1;
+    if (M.state != 0 || M.k >= M.max_iter) {
+      M.phase = FINISHED;
+      continue;
+    }
+    dir[b] = 1;
+    any_dir = true;
+  }
+  if (any_dir) {
+    for (int b = 0; b < B; ++b) {
+      A.mask()[b] = dir[b];
+      const int cnt = dir[b] ? (int)mb[b].pairs.size() : 0;
       A.cnt()[b] = cnt;
       for (int j = 0; j < cnt; ++j) {
         A.pslot()[(size_t)b * m + j] = mb[b].pairs[j];
@@ -239,10 +265,11 @@ da_status lbfgs_round(da_ctx* c, cudaStream_t st) {
     da::k_two_loop<<<B, da::kBlasThreads, 0, st>>>(dv);
     if ((r = check_launch(c))) return r;
     if ((r = read_scalars(c, st))) return r;
+    std::vector<double> gd(B, 0.0);
     bool reset = false;
     for (int b = 0; b < B; ++b) {
       A.mask()[b] = 0;
-      if (!active[b]) continue;
+      if (!dir[b]) continue;
       gd[b] = sc(b, da::SC_GD);
       if (!(gd[b] < 0.0)) {  // not a descent direction: restart from -g
         mb[b].pairs.clear();
@@ -258,104 +285,90 @@ da_status lbfgs_round(da_ctx* c, cudaStream_t st) {
       if ((r = check_launch(c))) return r;
     }
     for (int b = 0; b < B; ++b) {
-      if (!active[b]) continue;
+      if (!dir[b]) continue;
       Member& M = mb[b];
       const double s0 = M.k == 0 ? std::min(1.0, 1.0 / M.gnorm) : 1.0;
-      ls[b].start(M.f, gd[b], s0, M.c1, M.c2, 1e-10, 1e-20, 1e20, M.max_ls);
-      searching[b] = 1;
+      M.ls.start(M.f, gd[b], s0, M.c1, M.c2, 1e-10, 1e-20, 1e20, M.max_ls);
+      M.sub = SEARCHING;
       ++M.k;
     }
   }
-  // line search, all searching members together; the first evaluation also
-  // serves the started members
-  bool first = true;
-  for (;;) {
-    bool anys = false;
-    for (int b = 0; b < B; ++b) anys |= searching[b] != 0;
-    if (!anys && !(first && any_fresh)) break;
-    std::vector<char> live(B, 0);
-    for (int b = 0; b < B; ++b) {
-      live[b] = searching[b] || (first && fresh[b]);
-      A.mask()[b] = searching[b];
-      A.stp()[b] = searching[b] ? ls[b].stp() : 0.0;
-    }
-    if ((r = A.upload())) return r;
-    da::k_trial<<<ew, 256, 0, st>>>(dv);  // xt = x + stp d for searching members, x otherwise
-    if ((r = check_launch(c))) return r;
-    if ((r = cost_grad_members(c, XT, c->lb_J, GT, &live, st))) return r;
-    da::k_dot_gt_d<<<B, da::kBlasThreads, 0, st>>>(dv);
-    if ((r = check_launch(c))) return r;
-    if (first && any_fresh && (r = take_fresh())) return r;
-    if ((r = read_scalars(c, st))) return r;
-    if (first && any_fresh) record_fresh();
-    first = false;
-    bool accept_any = false;
-    for (int b = 0; b < B; ++b) A.mask()[b] = 0;
-    for (int b = 0; b < B; ++b) {
-      if (!searching[b]) continue;
-      Member& M = mb[b];
-      const double ft = hJ[b], dg = sc(b, da::SC_DG);
-      if (!std::isfinite(ft) || !std::isfinite(dg)) {
-        searching[b] = 0;
-        M.state = 3;
-        continue;
-      }
-      const int act = ls[b].step(ft, dg);
-      if (act == da::MoreThuente::EVALUATE) continue;
-      searching[b] = 0;
-      const bool ok = act == da::MoreThuente::CONVERGED;
-      if (ok || ft < M.f) {
-        // accept: the new pair goes to a free slot, s = xt - x, y = gt - g
-        int freeslot = 0;
-        for (int t = 0; t < slots; ++t)
-          if (std::find(M.pairs.begin(), M.pairs.end(), t) == M.pairs.end()) {
-            freeslot = t;
-            break;
-          }
-        M.pending = freeslot;
-        A.mask()[b] = 1;
-        A.aslot()[b] = freeslot;
-        accept_any = true;
-        M.f = ft;
-        M.iters = M.k;
-        M.hist.push_back(ft);
-      }
-      if (!ok) M.state = 2;
-    }
-    if (accept_any) {
-      if ((r = A.upload())) return r;
-      da::k_accept<<<B, da::kBlasThreads, 0, st>>>(dv);
-      if ((r = check_launch(c))) return r;
-    }
+
+  // 3. one shared evaluation: the searching members' trials, xt = x + stp d,
+  // and the first points of the newly started members, xt = x
+  std::vector<char> live(B, 0), searching(B, 0), fresh(B, 0);
+  bool any_live = false, any_fresh = false;
+  for (int b = 0; b < B; ++b) {
+    const Member& M = mb[b];
+    searching[b] = M.phase == ITERATING && M.sub == SEARCHING;
+    fresh[b] = M.phase == STARTED && M.sub == FIRST_EVAL;
+    live[b] = searching[b] || fresh[b];
+    any_live |= live[b] != 0;
+    any_fresh |= fresh[b] != 0;
+    A.mask()[b] = searching[b];
+    A.stp()[b] = searching[b] ? M.ls.stp() : 0.0;
   }
-  // end of the round: pair tests and gradient norms
-  da::k_gnorm2<<<B, da::kBlasThreads, 0, st>>>(dv);
+  if (!any_live) return DA_OK;
+  if ((r = A.upload())) return r;
+  da::k_trial<<<ew, 256, 0, st>>>(dv);
   if ((r = check_launch(c))) return r;
+  if ((r = cost_grad_members(c, XT, c->lb_J, GT, &live, st))) return r;
+  da::k_dot_gt_d<<<B, da::kBlasThreads, 0, st>>>(dv);
+  if ((r = check_launch(c))) return r;
+  if (any_fresh) {  // g = gt for the members just evaluated for the first time
+    for (int b = 0; b < B; ++b) A.mask()[b] = fresh[b];
+    if ((r = A.upload())) return r;
+    da::k_take_gradient<<<ew, 256, 0, st>>>(dv);
+    if ((r = check_launch(c))) return r;
+  }
   if ((r = read_scalars(c, st))) return r;
+
+  // 4. results
+  bool accept_any = false;
+  for (int b = 0; b < B; ++b) A.mask()[b] = 0;
   for (int b = 0; b < B; ++b) {
     Member& M = mb[b];
-    if (M.pending >= 0) {
-      const double sy = sc(b, da::SC_SY), yy = sc(b, da::SC_YY);
-      if (sy > 1e-16 * yy) {
-        if ((int)M.pairs.size() == m) {
-          M.pairs.erase(M.pairs.begin());
-          M.rho.erase(M.rho.begin());
-        }
-        M.pairs.push_back(M.pending);
-        M.rho.push_back(1.0 / sy);
-      }
-      M.pending = -1;
-    }
-    if (active[b] || fresh[b]) M.gnorm = std::sqrt(sc(b, da::SC_GG));
     if (fresh[b]) {
-      M.g0norm = M.gnorm;
-      M.phase = ITERATING;
-      if (!std::isfinite(M.f) || !std::isfinite(M.gnorm)) {
-        M.state = 3;
-        M.phase = FINISHED;
-      }
+      M.f = hJ[b];
+      M.hist.assign(1, hJ[b]);
+      M.sub = FIRST_NORM;
+      continue;
     }
-    if (active[b] && M.state != 0) M.phase = FINISHED;
+    if (!searching[b]) continue;
+    const double ft = hJ[b], dg = sc(b, da::SC_DG);
+    if (!std::isfinite(ft) || !std::isfinite(dg)) {
+      M.state = 3;
+      M.phase = FINISHED;
+      continue;
+    }
+    const int act = M.ls.step(ft, dg);
+    if (act == da::MoreThuente::EVALUATE) continue;
+    const bool ok = act == da::MoreThuente::CONVERGED;
+    if (!ok) M.state = 2;
+    if (ok || ft < M.f) {
+      // accept: the new pair goes to a free slot, s = xt - x, y = gt - g
+      int freeslot = 0;
+      for (int t = 0; t < slots; ++t)
+        if (std::find(M.pairs.begin(), M.pairs.end(), t) == M.pairs.end()) {
+          freeslot = t;
+          break;
+        }
+      M.pending = freeslot;
+      A.mask()[b] = 1;
+      A.aslot()[b] = freeslot;
+      accept_any = true;
+      M.f = ft;
+      M.iters = M.k;
+      M.hist.push_back(ft);
+      M.sub = ACCEPTED;
+    } else {
+      M.phase = FINISHED;
+    }
+  }
+  if (accept_any) {
+    if ((r = A.upload())) return r;
+    da::k_accept<<<B, da::kBlasThreads, 0, st>>>(dv);
+    if ((r = check_launch(c))) return r;
   }
   return DA_OK;
 }
@@ -391,7 +404,7 @@ extern "C" da_status da_lbfgs_iterate(da_ctx* c, int* running, void* stream) {
     if (running) *running = 0;
     return DA_OK;
   }
-  da_status r = lbfgs_round(c, (cudaStream_t)stream);
+  da_status r = lbfgs_step(c, (cudaStream_t)stream);
   if (r) return r;
   if (running) {
     int n = 0;
@@ -447,7 +460,7 @@ extern "C" da_status da_assimilate(da_ctx* c, double* s, int max_iter, const da_
     bool running = false;
     for (const Member& M : S.mb) running |= M.phase == STARTED || M.phase == ITERATING;
     if (!running) break;
-    if ((r = lbfgs_round(c, st))) return r;
+    if ((r = lbfgs_step(c, st))) return r;
   }
   bool diverged = false, failed = false;
   std::string who;

@@ -14,9 +14,10 @@ depend on what else runs (own context, deterministic kernels).
 `CoBatchServer` goes further and shares launches between jobs: per grid size
 one pool context holds a fixed number of member slots (a ragged batch, its
 memory allocated once); a job of that grid takes a free slot between two
-L-BFGS rounds of the pool and leaves it when it finishes, and every round is
-one lockstep iteration of all the pool's jobs, so their forward and adjoint
-sweeps run in the same launches (da_set_member, da_lbfgs_*).
+optimiser steps of the pool and leaves it when it finishes, and every step is
+one cost-and-gradient evaluation shared by all the pool's jobs, whatever
+point of their iterations they are at, so their forward and adjoint sweeps
+run in the same launches (da_set_member, da_lbfgs_*).
 
 Reports per job: arrival, admission and completion times; overall:
 solves/s, p50/p99 latency.  `FakeExecutor` replaces the GPU for tests of
@@ -269,10 +270,11 @@ class CoBatchServer:
     pools: {n: dict(slots=S, nsteps=max horizon, px=max probes per side,
     dt=..., ckpt_every=K)} -- one pool context per grid size, created once
     (forcing available, members switch it on or off).  Each pool runs on its
-    own host thread and CUDA stream: between rounds it admits the arrived
-    jobs of its grid into free slots (their windows, kernels, observations and
-    first guesses), runs one round (da_lbfgs_iterate: an L-BFGS iteration of
-    every member in shared launches), and retires the members that finished.
+    own host thread and CUDA stream: between steps it admits the arrived jobs
+    of its grid into free slots (their windows, kernels, observations and
+    first guesses), runs one step (da_lbfgs_iterate: one evaluation shared by
+    every member, whatever point of its iteration it is at), and retires the
+    members that finished.
     Plan variant `plan` on every pool, so a job's result equals its result in
     a batch-1 context on that variant; plan=None lets the autotuner pick each
     pool's variant for its slot count (results then equal the batch-1 ones to
