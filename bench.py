@@ -540,6 +540,36 @@ def run_workload(args):
         line.update({"metric": "fwd+adjoint gridpoint-steps/s FP64 per grid size and batch", "unit": UNIT,
                      "rows": rows, "config": {"flow": "decaying, nu 1e-3", "probes": "8x8 every 10 steps",
                                               "kernel": "exp_abs:0.5", "launch": "CUDA graph replay"}})
+    elif args.workload == "plain":
+        # the plain method: 64^2 decaying turbulence, 200 RK4 steps of 5e-3, nu = 1e-3, 8x8 probes every
+        # 10 steps (noise-free), W = exp(-0.5|k|), first guess from the t = 0 probes; one evaluation,
+        # then 10 L-BFGS iterations
+        n, nsteps = 64, 200
+        cfg = api.Config(n=n, nsteps=nsteps, dt=5e-3, nu=1e-3, px=8, every=10,
+                         kernels=[api.KernelSpec("exp_abs", 0.5)])
+        from paper_2602_14016_gb300 import synthetic
+
+        w_truth = synthetic.random_vorticity_hat(n, 0)
+        fwd = api.Context(api.Config(**{**cfg.__dict__, "store": False}))
+        _, obs = fwd.forward(fwd.control_from_omega(torch.from_numpy(w_truth[None]).cuda()))
+        fwd.close()
+        w_guess = workloads.first_guess_from_probes(w_truth, n, 8)
+        out = workloads.assimilation_run(api, torch, cfg, obs.cpu().numpy(), w_guess[None], w_truth[None],
+                                         args.assim_iters)
+        line.update({"metric": "plain-method assimilation: first evaluation and L-BFGS iterations", **out,
+                     "config": {"grid": n, "nsteps": nsteps, "dt": 5e-3, "nu": 1e-3, "probes": "8x8 every 10",
+                                "kernel": "exp_abs:0.5", "iters": args.assim_iters}})
+    elif args.workload == "sweep-assim":
+        # the kernel sweep's full assimilation: the headline window, every member run through
+        # --assim-iters L-BFGS iterations from the probe-interpolated first guess
+        kernels = SWEEP
+        dev = torch.device("cuda", 0)
+        m, w_guess, w_truth = prepare(api, torch, kernels, dev)
+        cfg = api.Config(n=W["n"], nsteps=W["nsteps"], dt=W["dt"], nu=W["nu"], forcing=W["forcing"], amp=W["amp"],
+                         nf=W["nf"], px=W["px"], every=W["every"], kernels=[api.KernelSpec(k, a) for k, a in kernels])
+        out = workloads.assimilation_run(api, torch, cfg, m, w_guess, w_truth[None], args.assim_iters)
+        line.update({"metric": "kernel-sweep assimilation (Sec. III.B): J and initial-condition error per kernel",
+                     **out, "config": {"workload": WORKLOAD_NAME, "iters": args.assim_iters}})
     elif args.workload == "fp64peak":
         with ClockSampler(0) as clk:
             probe = fp64_probe(iters=args.probe_iters)
@@ -604,8 +634,10 @@ def main():
     ap.add_argument("--no-graphs", dest="graphs", action="store_false")
     ap.add_argument("--tune-steps", type=int, default=8, help="RK steps per plan variant in the autotuner (0: off)")
     ap.add_argument("--probe-iters", type=int, default=100000, help="fp64peak: loop rounds per thread")
+    ap.add_argument("--assim-iters", type=int, default=None,
+                    help="plain / sweep-assim: L-BFGS iterations (defaults 10 and 100)")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "ensemble", "autograd", "serve", "grids",
-                                                            "fp64peak"],
+                                                            "fp64peak", "plain", "sweep-assim"],
                     help="sweep: the headline workload above; the others print their own line")
     ap.add_argument("--ens256", type=int, default=256)
     ap.add_argument("--ens512", type=int, default=64)
@@ -633,6 +665,8 @@ def main():
         ap.error("--window-steps must be a multiple of 20")
     W["nsteps"] = args.window_steps
     W["spinup_steps"] = args.spinup_steps
+    if args.assim_iters is None:
+        args.assim_iters = 10 if args.workload == "plain" else 100
     if args.impl == "reference":
         run_reference(args)
     elif args.workload != "sweep":
