@@ -304,7 +304,7 @@ class CoBatchServer:
                 for b in range(p["slots"]):
                     ctx.set_member(b, 0)
                 self.pools[n] = {"ctx": ctx, "slots": p["slots"], "stream": torch.cuda.Stream(device),
-                                 "jobs": [None] * p["slots"], "rounds": 0}
+                                 "jobs": [None] * p["slots"], "steps": 0}
         self.peak_members = 0
 
     @staticmethod
@@ -342,7 +342,7 @@ class CoBatchServer:
                         time.sleep(max(0.0, min(0.05, nxt - (time.perf_counter() - t0))))
                         continue
                     ctx.lbfgs_iterate(stream=st)
-                    pool["rounds"] += 1
+                    pool["steps"] += 1
                     for b, j in enumerate(slots):
                         if j is None:
                             continue
@@ -379,7 +379,7 @@ class CoBatchServer:
         if errors:
             raise RuntimeError(f"pool failures: {errors}")
         return summarize(jobs, peak_members=self.peak_members,
-                         rounds={int(n): p["rounds"] for n, p in self.pools.items()})
+                         steps={int(n): p["steps"] for n, p in self.pools.items()})
 
     def close(self):
         for p in self.pools.values():
