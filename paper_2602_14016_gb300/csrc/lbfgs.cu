@@ -50,7 +50,7 @@ struct Member {
   int max_iter = 0;
   int k = 0;                // iterations begun
   int iters = 0;            // iterations that accepted a step
-  int pending = -1;         // slot of a pair accepted in this round, tested at its end
+  int pending = -1;         // slot of a pair accepted by the last step, tested in the next
   double c1 = 1e-4, c2 = 0.9, gtol = 1e-10;
   int max_ls = 20;
   std::vector<int> pairs;   // slot indices, oldest first (at most `memory`)
