@@ -611,8 +611,15 @@ def run_workload(args):
                                job_cap=int(budget / args.slots)).run(fresh_jobs())
             base = serve.Server(serve.CudaExecutor(), memory_budget=budget, slots=1,
                                 job_cap=int(budget / args.slots)).run(fresh_jobs())
-            summary[str(rate)] = {"co_batched": out_co, "stream_overlap": out, "one_job_at_a_time": base,
-                                  "pools": {str(n): p for n, p in pools.items()}}
+            # hybrid: grids up to 256^2 co-batched in pools, larger ones as their own contexts
+            small = [n for n in args.serve_grids if n <= 256]
+            hy = serve.HybridServer({n: pools[n] for n in small}, big_budget=budget // 2, big_slots=2,
+                                    plan=None)
+            out_hy = hy.run(fresh_jobs())
+            hy.close()
+            torch.cuda.empty_cache()
+            summary[str(rate)] = {"co_batched": out_co, "hybrid": out_hy, "stream_overlap": out,
+                                  "one_job_at_a_time": base, "pools": {str(n): p for n, p in pools.items()}}
         line.update({"metric": "served solves/s, p50/p99 latency", "rates": summary,
                      "config": {"jobs": args.serve_jobs, "slots": args.slots, "co_slots": args.co_slots,
                                 "grids": args.serve_grids,

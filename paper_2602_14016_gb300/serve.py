@@ -384,3 +384,46 @@ class CoBatchServer:
     def close(self):
         for p in self.pools.values():
             p["ctx"].close()
+
+
+class HybridServer:
+    """Co-batching where it pays, own contexts where it does not.
+
+    A grid small enough that one member leaves most of the GPU idle gains
+    from sharing launches (CoBatchServer pools); a large grid fills the GPU
+    with one member, and its jobs run best as their own contexts overlapped
+    on streams (Server with CudaExecutor), with full trajectory storage when
+    it fits their memory cap.  Jobs are split by grid size between the two,
+    which run at the same time on the same GPU, each with its own memory
+    budget."""
+
+    def __init__(self, pools: dict, big_budget: int, big_slots: int = 2, big_job_cap: Optional[int] = None,
+                 device: int = 0, plan: Optional[int] = 0, every: int = 10):
+        self.co = CoBatchServer(pools, device=device, plan=plan, every=every)
+        self.big = Server(CudaExecutor(device), memory_budget=big_budget, slots=big_slots,
+                          job_cap=big_job_cap or big_budget // max(1, big_slots))
+
+    def run(self, jobs: list) -> dict:
+        small = [j for j in jobs if j.n in self.co.pools]
+        big = [j for j in jobs if j.n not in self.co.pools]
+        out, errors = {}, []
+
+        def go(name, srv, js):
+            try:
+                if js:
+                    out[name] = srv.run(js)
+            except Exception as e:  # recorded; the run reports it
+                errors.append((name, repr(e)))
+
+        th = [threading.Thread(target=go, args=("co", self.co, small)),
+              threading.Thread(target=go, args=("big", self.big, big))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        if errors:
+            raise RuntimeError(f"server failures: {errors}")
+        return summarize(jobs, co_batched_jobs=len(small), own_context_jobs=len(big))
+
+    def close(self):
+        self.co.close()

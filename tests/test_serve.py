@@ -142,3 +142,13 @@ def test_co_batched_results_equal_the_alone_results():
         assert j.status == a.status and j.iters_done == a.iters_done, (j.job_id, j.status, a.status)
         assert np.array_equal(j.J_hist, a.J_hist), (j.job_id, j.J_hist, a.J_hist)
         assert np.array_equal(j.s, a.s), j.job_id
+    # the hybrid server: 32^2 jobs co-batched, 64^2 jobs in their own contexts
+    mixed = [serve.Job(**{f.name: getattr(j, f.name) for f in serve.dataclasses.fields(serve.Job)}) for j in jobs]
+    for j in mixed:
+        j.s, j.J_hist, j.status = None, None, -1
+    hy = serve.HybridServer({32: dict(slots=2, nsteps=40, px=8, dt=5e-3)}, big_budget=1 << 34, big_slots=2, every=5)
+    out = hy.run(mixed)
+    hy.close()
+    assert out["failed"] == 0 and out["co_batched_jobs"] == 3 and out["own_context_jobs"] == 2
+    for a, j in zip(alone, mixed):
+        assert np.array_equal(j.J_hist, a.J_hist) and np.array_equal(j.s, a.s), j.job_id
