@@ -200,10 +200,17 @@ extern "C" da_status da_create(da_ctx** out, const da_grid* grid, double nu, con
     da_destroy(c);
     return DA_ECUDA;
   }
-  ops->make_mult(d, (double*)d.mult, d_kind, d_param, d_table, c->d_mnu, 0);
-  c->launches++;
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  // the multiplier on a stream of its own, waited for alone (a device-wide
+  // wait would also disturb other threads' work, e.g. a graph capture)
+  cudaStream_t mk = nullptr;
+  e = cudaStreamCreateWithFlags(&mk, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    ops->make_mult(d, (double*)d.mult, d_kind, d_param, d_table, c->d_mnu, mk);
+    c->launches++;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(mk);
+    cudaStreamDestroy(mk);
+  }
   std::vector<double> mult(comp);
   if (e == cudaSuccess) e = cudaMemcpy(mult.data(), d.mult, comp * sizeof(double), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) {
@@ -608,6 +615,7 @@ da_status cost_grad_members(da_ctx* c, const double* s, double* J, double* grad_
     da_ctx::CapturedEval* ce = nullptr;
     for (auto& g : c->cg_cache)
       if (g.steps == c->eval_steps) ce = &g;
+    bool direct = false;
     if (!ce) {
       cudaGraph_t g = nullptr;
       cudaGraphExec_t ex = nullptr;
@@ -615,24 +623,36 @@ da_status cost_grad_members(da_ctx* c, const double* s, double* J, double* grad_
       DA_TRY_CUDA(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
       r = enqueue_cost_grad(c, c->sbuf, c->gbuf, c->gstream);
       cudaError_t e = cudaStreamEndCapture(c->gstream, &g);
-      if (r) {
+      if (r || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
-        return r;
+        cudaGetLastError();
+        c->launches = l0;
+        // Another thread's device-wide synchronisation (a cudaFree, say)
+        // invalidates a capture in flight: nothing of it ran, so this
+        // evaluation runs by direct launches instead, and a later call
+        // captures again.
+        if (e != cudaErrorStreamCaptureInvalidated && (r != DA_ECUDA || e == cudaSuccess))
+          return r ? r : fail(c, DA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        direct = true;
+      } else {
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(c, DA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        if (c->cg_cache.size() >= kMaxCapturedEvals) {  // evict the oldest
+          cudaGraphExecDestroy(c->cg_cache.front().exec);
+          c->cg_cache.erase(c->cg_cache.begin());
+        }
+        c->cg_cache.push_back({c->eval_steps, ex, c->launches - l0});
+        c->launches = l0;
+        ce = &c->cg_cache.back();
       }
-      if (e != cudaSuccess) return fail(c, DA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&ex, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return fail(c, DA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-      if (c->cg_cache.size() >= kMaxCapturedEvals) {  // evict the oldest
-        cudaGraphExecDestroy(c->cg_cache.front().exec);
-        c->cg_cache.erase(c->cg_cache.begin());
-      }
-      c->cg_cache.push_back({c->eval_steps, ex, c->launches - l0});
-      c->launches = l0;
-      ce = &c->cg_cache.back();
     }
-    DA_TRY_CUDA(c, cudaGraphLaunch(ce->exec, c->gstream));
-    c->launches += ce->launches;
+    if (direct) {
+      if ((r = enqueue_cost_grad(c, c->sbuf, c->gbuf, c->gstream))) return r;
+    } else {
+      DA_TRY_CUDA(c, cudaGraphLaunch(ce->exec, c->gstream));
+      c->launches += ce->launches;
+    }
     c->have_fwd = c->ckpt == 0;
     DA_TRY_CUDA(c, cudaEventRecord(c->ev_out, c->gstream));
     DA_TRY_CUDA(c, cudaStreamWaitEvent(st, c->ev_out, 0));
