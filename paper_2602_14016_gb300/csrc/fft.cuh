@@ -172,27 +172,10 @@ template <> struct Plan<512, 2> { using two = Radices<8, 8, 8>; using one = Radi
 template <> struct Plan<1024, 0> { using two = Radices<16, 8, 8>; using one = Radices<16, 8, 8>; static constexpr int threads = 256; };
 template <> struct Plan<1024, 1> { using two = Radices<16, 4, 4, 4>; using one = Radices<16, 4, 4, 4>; static constexpr int threads = 256; };
 template <> struct Plan<1024, 2> { using two = Radices<8, 8, 4, 4>; using one = Radices<8, 8, 4, 4>; static constexpr int threads = 256; };
-// Component-split plans: two adjacent lanes share each butterfly, one for the
-// real and one for the imaginary parts of its outputs (a multiplication by
-// +-i takes the partner's component by a lane shuffle).  The FP64
-// instructions are those of the unsplit plan, split evenly, and the results
-// are bitwise the same; each thread's chain is half as long and a CTA has
-// twice the warps, for the passes that have too few CTAs to fill the GPU
-// (the column passes, small grids).
-template <> struct Plan<32, 2> { using two = Radices<2, 2, 2, 2, 2>; using one = Radices<2, 2, 2, 2, 2>; static constexpr int threads = 64; };
-template <> struct Plan<64, 3> { using two = Radices<2, 2, 2, 2, 2, 2>; using one = Radices<2, 2, 2, 2, 2, 2>; static constexpr int threads = 128; };
-template <> struct Plan<128, 4> { using two = Radices<2, 2, 2, 2, 2, 2, 2>; using one = Radices<2, 2, 2, 2, 2, 2, 2>; static constexpr int threads = 256; };
-template <> struct Plan<256, 3> { using two = Radices<4, 4, 4, 4>; using one = Radices<4, 4, 4, 4>; static constexpr int threads = 256; };
-
-template <int N, int V> struct PlanSplit { static constexpr bool value = false; };
-template <> struct PlanSplit<32, 2> { static constexpr bool value = true; };
-template <> struct PlanSplit<64, 3> { static constexpr bool value = true; };
-template <> struct PlanSplit<128, 4> { static constexpr bool value = true; };
-template <> struct PlanSplit<256, 3> { static constexpr bool value = true; };
 
 // Number of plan variants of each size (the instantiations in inst_n*.cu).
 constexpr int plan_count(int n) {
-  return n == 32 ? 3 : n == 64 ? 4 : n == 128 ? 5 : n == 256 ? 4 : (n == 512 || n == 1024) ? 3 : 1;
+  return n == 32 ? 2 : n == 64 ? 3 : n == 128 ? 4 : (n == 256 || n == 512 || n == 1024) ? 3 : 1;
 }
 
 template <int N, int V = 0>
@@ -404,99 +387,12 @@ __device__ __forceinline__ void stockham_stage_folded(double2* buf, const double
   __syncthreads();
 }
 
-// One in-place Stockham stage of a component-split plan (radix 2 or 4,
-// folded twiddles): thread u takes component u & 1 of butterfly u >> 1.
-// Every lane of a warp runs the loop and the shuffle, active or not.
-template <int N, int V, int R, int S, int F, int L>
-__device__ __forceinline__ void stockham_stage_split(double2* buf, const double* __restrict__ T) {
-  static_assert(R == 2 || R == 4, "component-split stages of radix 2 and 4");
-  constexpr int NB = N / R, Th = PlanInfo<N, V>::THREADS, TOT = 2 * F * NB, J = (TOT + Th - 1) / Th;
-  double* bd = reinterpret_cast<double*>(buf);
-  const int c = threadIdx.x & 1;
-  const double sg = S < 0 ? 1.0 : -1.0;          // sign of the stored tangents
-  const double sgi = c == 0 ? -(double)S : (double)S;  // component c of (S i) x: sgi x_{other}
-  double o[J][R];
-  int pos[J];
-#pragma unroll
-  for (int jb = 0; jb < J; ++jb) {
-    const int u = threadIdx.x + jb * Th;
-    const bool on = TOT % Th == 0 || u < TOT;
-    const int bf = on ? u >> 1 : 0;
-    const int f = bf / NB, i = bf - f * NB, k = i & (L - 1);
-    const int base = f * N;
-    pos[jb] = base + (i - k) * R + k;
-    double a0 = 0.0;
-    double2 a[R];
-#pragma unroll
-    for (int m = 0; m < R; ++m) a[m] = make_double2(0.0, 0.0);
-    if (on) {
-      a0 = bd[2 * (base + i) + c];
-#pragma unroll
-      for (int m = 1; m < R; ++m) a[m] = buf[base + i + m * NB];
-    }
-    // component c of a[m], and of a[m] rotated by its folded twiddle (tangent t)
-    auto comp = [&](int m) { return c == 0 ? a[m].x : a[m].y; };
-    auto rot = [&](int m, double t) { return c == 0 ? fma(-t, a[m].y, a[m].x) : fma(t, a[m].x, a[m].y); };
-    if constexpr (R == 2) {
-      if constexpr (L == 1) {
-        o[jb][0] = a0 + comp(1);
-        o[jb][1] = a0 - comp(1);
-      } else {
-        const double z1 = rot(1, sg * T[k]), c1 = T[L + k];
-        o[jb][0] = fma(c1, z1, a0);
-        o[jb][1] = fma(-c1, z1, a0);
-      }
-    } else {
-      double t0, t1, p, q, c1 = 1.0;
-      if constexpr (L == 1) {
-        t0 = a0 + comp(2);
-        t1 = a0 - comp(2);
-        p = comp(1) + comp(3);
-        q = comp(1) - comp(3);  // the partner's q times +-1 is this component of (S i)(a1 - a3)
-      } else {
-        const double z1 = rot(1, sg * T[k]), z2 = rot(2, sg * T[L + k]), z3 = rot(3, sg * T[2 * L + k]);
-        c1 = T[3 * L + k];
-        const double c2 = T[4 * L + k], r31 = T[5 * L + k];
-        t0 = fma(c2, z2, a0);
-        t1 = fma(-c2, z2, a0);
-        p = fma(r31, z3, z1);
-        q = fma(-r31, z3, z1);
-      }
-      const double w = sgi * __shfl_xor_sync(0xffffffffu, q, 1);
-      if constexpr (L == 1) {
-        o[jb][0] = t0 + p;
-        o[jb][2] = t0 - p;
-        o[jb][1] = t1 + w;
-        o[jb][3] = t1 - w;
-      } else {
-        o[jb][0] = fma(c1, p, t0);
-        o[jb][2] = fma(-c1, p, t0);
-        o[jb][1] = fma(c1, w, t1);
-        o[jb][3] = fma(-c1, w, t1);
-      }
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int jb = 0; jb < J; ++jb) {
-    const int u = threadIdx.x + jb * Th;
-    if (TOT % Th == 0 || u < TOT) {
-#pragma unroll
-      for (int m = 0; m < R; ++m) bd[2 * (pos[jb] + m * L) + c] = o[jb][m];
-    }
-  }
-  __syncthreads();
-}
-
 template <int N, int V, int S, int F, int L>
 __device__ __forceinline__ void run_stages_folded(double2*, const double*, Radices<>) {}
 
 template <int N, int V, int S, int F, int L, int R, int... Rs>
 __device__ __forceinline__ void run_stages_folded(double2* buf, const double* T, Radices<R, Rs...>) {
-  if constexpr (PlanSplit<N, V>::value)
-    stockham_stage_split<N, V, R, S, F, L>(buf, T);
-  else
-    stockham_stage_folded<N, V, R, S, F, L>(buf, T);
+  stockham_stage_folded<N, V, R, S, F, L>(buf, T);
   run_stages_folded<N, V, S, F, L * R>(buf, T + (L > 1 ? FoldSlots<R>::value * L : 0), Radices<Rs...>{});
 }
 

@@ -119,9 +119,8 @@ struct Geo {
   static constexpr int PMAX = 64;
   static constexpr size_t SMEM = sizeof(double) * FoldInfo<N, V>::PADDED + sizeof(double2) * (2 * N + 2 * PMAX);
   // column passes load their epilogue inputs before the transforms (about
-  // 60 more registers a thread) where a CTA is at most 128 threads or a
-  // thread has a single mode of the column
-  static constexpr bool PREFETCH = THREADS <= 128 || Kr <= THREADS;
+  // 60 more registers a thread) where a CTA is at most 128 threads
+  static constexpr bool PREFETCH = THREADS <= 128;
 };
 
 __device__ __forceinline__ int ky_of_row(int r, int K) { return r <= K ? r : r - (2 * K + 1); }

@@ -33,20 +33,16 @@ struct Ops {
 const Ops* ops_n16_v0();
 const Ops* ops_n32_v0();
 const Ops* ops_n32_v1();
-const Ops* ops_n32_v2();
 const Ops* ops_n64_v0();
 const Ops* ops_n64_v1();
 const Ops* ops_n64_v2();
-const Ops* ops_n64_v3();
 const Ops* ops_n128_v0();
 const Ops* ops_n128_v1();
 const Ops* ops_n128_v2();
 const Ops* ops_n128_v3();
-const Ops* ops_n128_v4();
 const Ops* ops_n256_v0();
 const Ops* ops_n256_v1();
 const Ops* ops_n256_v2();
-const Ops* ops_n256_v3();
 const Ops* ops_n512_v0();
 const Ops* ops_n512_v1();
 const Ops* ops_n512_v2();
@@ -59,11 +55,10 @@ inline const Ops* ops_for(int n, int v = 0) {
   if (v < 0 || v >= plan_count(n)) return nullptr;
   switch (n) {
     case 16: return ops_n16_v0();
-    case 32: return v == 0 ? ops_n32_v0() : v == 1 ? ops_n32_v1() : ops_n32_v2();
-    case 64: return v == 0 ? ops_n64_v0() : v == 1 ? ops_n64_v1() : v == 2 ? ops_n64_v2() : ops_n64_v3();
-    case 128:
-      return v == 0 ? ops_n128_v0() : v == 1 ? ops_n128_v1() : v == 2 ? ops_n128_v2() : v == 3 ? ops_n128_v3() : ops_n128_v4();
-    case 256: return v == 0 ? ops_n256_v0() : v == 1 ? ops_n256_v1() : v == 2 ? ops_n256_v2() : ops_n256_v3();
+    case 32: return v == 0 ? ops_n32_v0() : ops_n32_v1();
+    case 64: return v == 0 ? ops_n64_v0() : v == 1 ? ops_n64_v1() : ops_n64_v2();
+    case 128: return v == 0 ? ops_n128_v0() : v == 1 ? ops_n128_v1() : v == 2 ? ops_n128_v2() : ops_n128_v3();
+    case 256: return v == 0 ? ops_n256_v0() : v == 1 ? ops_n256_v1() : ops_n256_v2();
     case 512: return v == 0 ? ops_n512_v0() : v == 1 ? ops_n512_v1() : ops_n512_v2();
     case 1024: return v == 0 ? ops_n1024_v0() : v == 1 ? ops_n1024_v1() : ops_n1024_v2();
     default: return nullptr;

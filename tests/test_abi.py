@@ -83,7 +83,7 @@ def test_invalid_problems_are_rejected_on_the_host(lib, kw, frag):
 def test_plan_variant_queries_on_the_host(lib):
     """Plan counts per supported size, 0 elsewhere; NULL contexts are rejected
     before any device work."""
-    counts = {16: 1, 32: 3, 64: 4, 128: 5, 256: 4, 512: 3, 1024: 3}
+    counts = {16: 1, 32: 2, 64: 3, 128: 4, 256: 3, 512: 3, 1024: 3}
     for n, c in counts.items():
         assert lib.da_plan_count(n) == c
     for n in (0, 8, 48, 100, 2048):
