@@ -132,30 +132,32 @@ def hbm_fraction(traffic, avg_ms):
     return {"achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak, "peak_source": src}
 
 
-def fft_flops(n: int) -> float:
-    """Nominal flops of one complex length-n FFT (5 n log2 n)."""
-    return 5.0 * n * np.log2(n)
+def pass_flops(n: int, batch: int, variant: int = 0) -> dict:
+    """Algorithmic FP64 flops per launch of each pass kernel: the nominal
+    count of the transforms it performs plus its pointwise arithmetic.  A
+    transform counts 5 n log2 n less the operations the kernels skip on the
+    gap of the 2/3 rule under this plan variant (da_plan_flops: zero inputs
+    of an inverse transform's first stage, unused outputs of a forward
+    transform's last stage)."""
+    from paper_2602_14016_gb300 import api
 
-
-def pass_flops(n: int, batch: int) -> dict:
-    """Algorithmic FP64 flops per launch of each pass kernel (nominal FFT
-    count of the transforms it performs plus its pointwise arithmetic)."""
     K = (n - 1) // 3
     Kc, Kr = K + 1, 2 * K + 1
-    f = fft_flops(n)
-    # rows: two packed complex transforms per row (inverse of u + i v, or of
-    # the adjoint fields a + i b, and forward of the two products); columns:
-    # two forward and two inverse transforms per retained column kx
+    fi, ff = api.plan_flops(n, variant)
+    # rows: per row pair one inverse transform of the packed pair (u + i v,
+    # or the adjoint fields a + i b) per row and one forward transform of the
+    # two products per row; columns: two forward and two inverse transforms
+    # per retained column kx
     return {
-        "fwd_rows": batch * (2.0 * n * f + 4.0 * n * n),
-        "fwd_cols": batch * (4.0 * Kc * f + 26.0 * Kr * Kc),
-        "adj_rows": batch * (2.0 * n * f + 8.0 * n * n),
-        "adj_cols": batch * (4.0 * Kc * f + 32.0 * Kr * Kc),
+        "fwd_rows": batch * (n * (fi + ff) + 4.0 * n * n),
+        "fwd_cols": batch * (2.0 * Kc * (fi + ff) + 26.0 * Kr * Kc),
+        "adj_rows": batch * (n * (fi + ff) + 8.0 * n * n),
+        "adj_cols": batch * (2.0 * Kc * (fi + ff) + 32.0 * Kr * Kc),
     }
 
 
-def flops_per_gridpoint_step(n: int) -> float:
-    p = pass_flops(n, 1)
+def flops_per_gridpoint_step(n: int, variant: int = 0) -> float:
+    p = pass_flops(n, 1, variant)
     return 4.0 * sum(p.values()) / (n * n)
 
 
@@ -354,6 +356,7 @@ def run_gpu(args):
     e_ms = e0.elapsed_time(e1)
     e2e_value = replicas.whole_job_rate(B * n * n * nsteps * e_steps, e_ms / 1e3, device)
 
+    plan = ctx.plan  # the batch context is freed before the plain path runs
     # the plain one-job-per-launch path: the same members one at a time
     plain = None
     if rank == 0 and args.plain:
@@ -383,7 +386,7 @@ def run_gpu(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    pf = pass_flops(n, B)[dom]
+    pf = pass_flops(n, B, plan)[dom]
     avg_ms = dom_ms / max(dom_n, 1)
     achieved = pf / (avg_ms / 1e3) / 1e9
     probe = fp64_probe((0, 1), iters=50000)
@@ -419,8 +422,8 @@ def run_gpu(args):
                      "roofline_pass_ms_per_step": roof_pass_ms,
                      "class_ms_warmup": {k: v[0] for k, v in class_ms.items()},
                      "hbm": hbm_fraction(traffic, avg_ms), "peak_derivation": peak, "fp64_probe": probe},
-        "flops_per_gridpoint_step": flops_per_gridpoint_step(n),
-        "achieved_gflops_step": value * flops_per_gridpoint_step(n) / 1e9,
+        "flops_per_gridpoint_step": flops_per_gridpoint_step(n, plan),
+        "achieved_gflops_step": value * flops_per_gridpoint_step(n, plan) / 1e9,
         "cpu_baseline": cpu,
         "plain_path": plain,
         "fft_plan": tune,

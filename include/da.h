@@ -221,6 +221,18 @@ da_status da_set_plan(da_ctx* ctx, int variant);
  * da_set_observations are kept).  DA_EINVAL for steps < 1. */
 da_status da_autotune(da_ctx* ctx, int steps, int* chosen, double* ms_per_step);
 
+/* Nominal flops of one band-limited transform of n points as the pass
+ * kernels run it under plan variant `variant` (Sec. II.B: the 2/3 rule keeps
+ * |kx|, |ky| <= K = (n-1)/3): 5 n log2 n less the operations they skip,
+ * namely the additions of the first stage that a zero input of the gap
+ * K < q < n - K would enter (inverse transforms, whose inputs are zero
+ * there) and the last-stage outputs in the gap (forward transforms, read
+ * back only on the band).  A skip counts only where it holds for all 32
+ * lanes of a warp.  inverse, forward: HOST double, one value each.  Host
+ * only, no device work; DA_EINVAL (message via da_last_error(NULL)) for an
+ * unsupported size or variant or a NULL pointer. */
+da_status da_plan_flops(int n, int variant, double* inverse, double* forward);
+
 /* Optional extra outputs of the last da_cost_grad / da_adjoint_terminal on
  * this context: lam0 [batch][n][n/2+1] complex, the DFT of grad_{w0} J
  * (the physical adjoint at t = 0, Eq. 12); filtered [batch][n][n] the

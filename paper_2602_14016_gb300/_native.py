@@ -21,7 +21,7 @@ KERNEL_KINDS = {"identity": 0, "exp_abs": 1, "frac": 2, "exp_sq": 3, "table": 4}
 
 # Entry points declared in include/da.h, in order.
 EXPORTS = ("da_create", "da_set_sobolev", "da_set_graphs", "da_plan_count", "da_get_plan", "da_set_plan", "da_autotune",
-           "da_set_observations", "da_forward", "da_cost_grad", "da_vjp", "da_last_adjoint",
+           "da_plan_flops", "da_set_observations", "da_forward", "da_cost_grad", "da_vjp", "da_last_adjoint",
            "da_adjoint_terminal", "da_adjoint_spectra", "da_num_shells", "da_assimilate", "da_set_member",
            "da_lbfgs_start", "da_lbfgs_iterate", "da_lbfgs_member", "da_lbfgs_release", "da_omega_from_control",
            "da_control_from_omega",
@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
             "da_get_plan": (I, [C]),
             "da_set_plan": (I, [C, I]),
             "da_autotune": (I, [C, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+            "da_plan_flops": (I, [I, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
             "da_set_observations": (I, [C, P, P]),
             "da_forward": (I, [C, P, P, P, P]),
             "da_cost_grad": (I, [C, P, P, P, P]),

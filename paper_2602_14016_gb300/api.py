@@ -63,6 +63,17 @@ def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p | None:
     return ctypes.c_void_p(t.data_ptr())
 
 
+def plan_flops(n: int, variant: int = 0) -> tuple[float, float]:
+    """Nominal flops of one band-limited (inverse, forward) transform of n
+    points as the pass kernels run it under plan `variant` (da_plan_flops)."""
+    lib = N.load()
+    inv, fwd = ctypes.c_double(), ctypes.c_double()
+    st = lib.da_plan_flops(int(n), int(variant), ctypes.byref(inv), ctypes.byref(fwd))
+    if st != N.DA_OK:
+        raise N.DAError(st, (lib.da_last_error(None) or b"").decode())
+    return inv.value, fwd.value
+
+
 class AssimResult(NamedTuple):
     J_hist: "object"  # numpy [B, max_iter+1]
     iters: "object"  # numpy int32 [B]

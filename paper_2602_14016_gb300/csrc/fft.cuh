@@ -39,22 +39,53 @@ __device__ __forceinline__ double2 mul_si(double2 a) {
   return S > 0 ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
 }
 
-// X_k = sum_m a_m exp(S 2 pi i m k / R), in place, natural order.
-template <int S>
-__device__ __forceinline__ void dft4(double2* a) {
-  const double2 t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
-  const double2 t2 = cadd(a[1], a[3]), t3 = mul_si<S>(csub(a[1], a[3]));
-  a[0] = cadd(t0, t2);
-  a[2] = csub(t0, t2);
-  a[1] = cadd(t1, t3);
-  a[3] = csub(t1, t3);
+// x + y and x - y where ZX, ZY mark an operand known to be zero: a first-stage
+// input in the gap of a band-limited sequence, whose load was skipped (its
+// register holds nothing).  A known zero costs no FP64 instruction.
+template <bool ZX, bool ZY>
+__device__ __forceinline__ double2 add_z(double2 x, double2 y) {
+  if constexpr (ZX && ZY) return make_double2(0.0, 0.0);
+  else if constexpr (ZY) return x;
+  else if constexpr (ZX) return y;
+  else return cadd(x, y);
+}
+template <bool ZX, bool ZY>
+__device__ __forceinline__ double2 sub_z(double2 x, double2 y) {
+  if constexpr (ZX && ZY) return make_double2(0.0, 0.0);
+  else if constexpr (ZY) return x;
+  else if constexpr (ZX) return make_double2(-y.x, -y.y);
+  else return csub(x, y);
 }
 
-template <int S>
+// Bits 0, 2, 4, ... (even) or 1, 3, 5, ... (odd) of a zero mask of r inputs,
+// packed: the masks of the two half-length DFTs of an even/odd split.
+__host__ __device__ constexpr int even_bits(int z, int r) {
+  int o = 0;
+  for (int j = 0; j < r / 2; ++j) o |= ((z >> (2 * j)) & 1) << j;
+  return o;
+}
+__host__ __device__ constexpr int odd_bits(int z, int r) { return even_bits(z >> 1, r); }
+
+// X_k = sum_m a_m exp(S 2 pi i m k / R), in place, natural order.  Bit m of
+// Z marks input m as zero (not loaded); Z = 0 is the plain DFT.
+template <int S, int Z = 0>
+__device__ __forceinline__ void dft4(double2* a) {
+  constexpr bool z0 = Z & 1, z1 = (Z >> 1) & 1, z2 = (Z >> 2) & 1, z3 = (Z >> 3) & 1;
+  constexpr bool ze = z0 && z2, zo = z1 && z3;
+  const double2 t0 = add_z<z0, z2>(a[0], a[2]), t1 = sub_z<z0, z2>(a[0], a[2]);
+  const double2 t2 = add_z<z1, z3>(a[1], a[3]), t3 = mul_si<S>(sub_z<z1, z3>(a[1], a[3]));
+  a[0] = add_z<ze, zo>(t0, t2);
+  a[2] = sub_z<ze, zo>(t0, t2);
+  a[1] = add_z<ze, zo>(t1, t3);
+  a[3] = sub_z<ze, zo>(t1, t3);
+}
+
+template <int S, int Z = 0>
 __device__ __forceinline__ void dft2(double2* a) {
+  constexpr bool z0 = Z & 1, z1 = (Z >> 1) & 1;
   const double2 t = a[0];
-  a[0] = cadd(t, a[1]);
-  a[1] = csub(t, a[1]);
+  a[0] = add_z<z0, z1>(t, a[1]);
+  a[1] = sub_z<z0, z1>(t, a[1]);
 }
 
 // cos(pi/4), cos(pi/8), tan(pi/8)
@@ -73,12 +104,12 @@ __device__ __forceinline__ void bfly_scaled(const double2 e, const double2 z, do
 // c (1 + i t) (or c (t + i)) with a constant tangent t, so that w o = c z
 // with z two FMAs (or two adds when t = 1), and e +- w o = e +- c z costs
 // four FMAs: six FP64 instructions instead of eight.
-template <int S>
+template <int S, int Z = 0>
 __device__ __forceinline__ void dft8(double2* a) {
   double2 e[4] = {a[0], a[2], a[4], a[6]};
   double2 o[4] = {a[1], a[3], a[5], a[7]};
-  dft4<S>(e);
-  dft4<S>(o);
+  dft4<S, even_bits(Z, 8)>(e);
+  dft4<S, odd_bits(Z, 8)>(o);
   // k = 0
   a[0] = cadd(e[0], o[0]);
   a[4] = csub(e[0], o[0]);
@@ -94,7 +125,7 @@ __device__ __forceinline__ void dft8(double2* a) {
   bfly_scaled(e[3], z3, -kR2, a[3], a[7]);
 }
 
-template <int S>
+template <int S, int Z = 0>
 __device__ __forceinline__ void dft16(double2* a) {
   double2 e[8], o[8];
 #pragma unroll
@@ -102,8 +133,8 @@ __device__ __forceinline__ void dft16(double2* a) {
     e[k] = a[2 * k];
     o[k] = a[2 * k + 1];
   }
-  dft8<S>(e);
-  dft8<S>(o);
+  dft8<S, even_bits(Z, 16)>(e);
+  dft8<S, odd_bits(Z, 16)>(o);
   // k = 0 and k = 4 (w = S i)
   a[0] = cadd(e[0], o[0]);
   a[8] = csub(e[0], o[0]);
@@ -127,12 +158,12 @@ __device__ __forceinline__ void dft16(double2* a) {
   bfly_scaled(e[7], z7, kC8, a[7], a[15]);
 }
 
-template <int R, int S>
+template <int R, int S, int Z = 0>
 __device__ __forceinline__ void dftR(double2* a) {
-  if constexpr (R == 2) dft2<S>(a);
-  if constexpr (R == 4) dft4<S>(a);
-  if constexpr (R == 8) dft8<S>(a);
-  if constexpr (R == 16) dft16<S>(a);
+  if constexpr (R == 2) dft2<S, Z>(a);
+  if constexpr (R == 4) dft4<S, Z>(a);
+  if constexpr (R == 8) dft8<S, Z>(a);
+  if constexpr (R == 16) dft16<S, Z>(a);
 }
 
 // Radix plans: a list of stage radices whose product is N.
@@ -292,17 +323,26 @@ __device__ __forceinline__ void fma_pair(double2 e, double2 z, double c, double2
   minus = make_double2(fma(-c, z.x, e.x), fma(-c, z.y, e.y));
 }
 
+// e + c z into plus unless output p is masked, e - c z into minus unless
+// output q is: the last stage of a forward transform leaves the outputs that
+// fall in the gap unformed (the compiler drops what only they would use).
+template <int O, int p, int q>
+__device__ __forceinline__ void fma_pair_o(double2 e, double2 z, double c, double2& plus, double2& minus) {
+  if constexpr (!((O >> p) & 1)) plus = make_double2(fma(c, z.x, e.x), fma(c, z.y, e.y));
+  if constexpr (!((O >> q) & 1)) minus = make_double2(fma(-c, z.x, e.x), fma(-c, z.y, e.y));
+}
+
 // Twiddled radix-2 butterfly with a folded twiddle: a0 +- c1 z1, six FP64
-// instructions.
-template <int S>
+// instructions.  Bit m of O: output m is not needed (left unformed).
+template <int S, int O = 0>
 __device__ __forceinline__ void dft2_folded(double2* a, const double* T, int k, int L) {
   const double sg = S < 0 ? 1.0 : -1.0;
   const double2 z1 = tan_rot(a[1], sg * T[k]);
-  fma_pair(a[0], z1, T[L + k], a[0], a[1]);
+  fma_pair_o<O, 0, 1>(a[0], z1, T[L + k], a[0], a[1]);
 }
 
 // Twiddled radix-4 butterfly with folded twiddles (table T, class k, L).
-template <int S>
+template <int S, int O = 0>
 __device__ __forceinline__ void dft4_folded(double2* a, const double* T, int k, int L) {
   const double sg = S < 0 ? 1.0 : -1.0;
   const double t1 = sg * T[k], t2 = sg * T[L + k], t3 = sg * T[2 * L + k];
@@ -311,12 +351,12 @@ __device__ __forceinline__ void dft4_folded(double2* a, const double* T, int k, 
   double2 t0, tt1, u, v;
   fma_pair(a[0], z2, c2, t0, tt1);
   fma_pair(z1, z3, r31, u, v);
-  fma_pair(t0, u, c1, a[0], a[2]);
-  fma_pair(tt1, mul_si<S>(v), c1, a[1], a[3]);
+  fma_pair_o<O, 0, 2>(t0, u, c1, a[0], a[2]);
+  fma_pair_o<O, 1, 3>(tt1, mul_si<S>(v), c1, a[1], a[3]);
 }
 
 // Twiddled radix-8 butterfly with folded twiddles.
-template <int S>
+template <int S, int O = 0>
 __device__ __forceinline__ void dft8_folded(double2* a, const double* T, int k, int L) {
   const double sg = S < 0 ? 1.0 : -1.0;
   double2 z[8];
@@ -338,39 +378,167 @@ __device__ __forceinline__ void dft8_folded(double2* a, const double* T, int k, 
   fma_pair(ou0, ou1, r31, p0, p2);
   fma_pair(ov0, mul_si<S>(ov1), r31, p1, p3);
   // a_k = e_k + W8^k c1 p_k
-  fma_pair(e0, p0, c1, a[0], a[4]);
-  fma_pair(e2, mul_si<S>(p2), c1, a[2], a[6]);
+  fma_pair_o<O, 0, 4>(e0, p0, c1, a[0], a[4]);
+  fma_pair_o<O, 2, 6>(e2, mul_si<S>(p2), c1, a[2], a[6]);
   const double2 w1 = make_double2(p1.x - S * p1.y, p1.y + S * p1.x);
-  fma_pair(e1, w1, q, a[1], a[5]);
+  fma_pair_o<O, 1, 5>(e1, w1, q, a[1], a[5]);
   const double2 w3 = make_double2(p3.x + S * p3.y, p3.y - S * p3.x);
-  fma_pair(e3, w3, -q, a[3], a[7]);
+  fma_pair_o<O, 3, 7>(e3, w3, -q, a[3], a[7]);
+}
+
+// ---------------------------------------------------------------------------
+// Band-limited sequences
+// ---------------------------------------------------------------------------
+//
+// The inverse transforms of the pass kernels read sequences that are zero in
+// the gap K < q < N - K (the 2/3 rule, K = (N-1)/3), and their forward
+// transforms are read back only on the band q <= K, q >= N - K.  Input m of
+// butterfly i of the first stage is x[i + m N/R]; output m of butterfly k of
+// the last stage is y[k + m N/R].  Where that position lies in the gap for
+// all 32 lanes of a warp, the warp skips the load and the additions the zero
+// would enter (first stage), or neither forms nor stores the output (last
+// stage; the buffer keeps whatever it held there).  The tests are per warp
+// because GB300's FP64 pipe spends the same time on a warp instruction
+// whatever its active lanes: only whole warp instructions saved count.  A
+// warp covers 32 consecutive butterflies of one sequence when N/R is a
+// multiple of 32; otherwise only the positions in the gap for every
+// butterfly are skipped.
+
+// positions lo..hi all in the gap of band kb (kb < 0: no band)
+__host__ __device__ constexpr bool in_gap(int n, int kb, int lo, int hi) {
+  return kb >= 0 && lo >= kb + 1 && hi <= n - kb - 1;
+}
+// m whose position is in the gap for every butterfly of a stage of radix r
+__host__ __device__ constexpr int gap_common(int n, int r, int kb) {
+  int c = 0;
+  for (int m = 0; m < r; ++m)
+    if (in_gap(n, kb, m * (n / r), m * (n / r) + n / r - 1)) c |= 1 << m;
+  return c;
+}
+// m in the gap for all lanes of some warps only
+__host__ __device__ constexpr int gap_per_warp(int n, int r, int kb) {
+  const int nb = n / r;
+  int c = 0;
+  if (nb % 32) return 0;
+  for (int m = 0; m < r; ++m)
+    for (int i0 = 0; i0 < nb; i0 += 32)
+      if (!((gap_common(n, r, kb) >> m) & 1) && in_gap(n, kb, i0 + m * nb, i0 + 31 + m * nb)) c |= 1 << m;
+  return c;
+}
+__host__ __device__ constexpr int bit_index(int b) {
+  int m = 0;
+  while (b > 1) {
+    b >>= 1;
+    ++m;
+  }
+  return m;
+}
+__host__ __device__ constexpr int popcount_c(int b) {
+  int c = 0;
+  for (; b; b &= b - 1) ++c;
+  return c;
+}
+
+template <int N, int R, int KB>
+struct GapMask {
+  static constexpr int NB = N / R;
+  static constexpr int C = gap_common(N, R, KB), X = gap_per_warp(N, R, KB);
+  static constexpr int A = X & -X, B = X & ~A;  // the per-warp bits
+  static_assert((B & (B - 1)) == 0, "at most two per-warp gap positions per butterfly");
+  // mask of the warp that holds butterfly i
+  __host__ __device__ static int warp(int i) {
+    int w = C;
+    if constexpr (A != 0) {
+      const int i0 = i & ~31;
+      constexpr int ma = bit_index(A);
+      if (in_gap(N, KB, i0 + ma * NB, i0 + 31 + ma * NB)) w |= A;
+      if constexpr (B != 0) {
+        constexpr int mb = bit_index(B);
+        if (in_gap(N, KB, i0 + mb * NB, i0 + 31 + mb * NB)) w |= B;
+      }
+    }
+    return w;
+  }
+};
+
+// The butterfly of one stage: untwiddled with zero inputs Z (first stage),
+// or twiddled with unneeded outputs O.
+template <int R, int S, int L, int Z, int O>
+__device__ __forceinline__ void stage_butterfly(double2* a, const double* T, int k) {
+  if constexpr (L == 1) {
+    static_assert(O == 0, "a first stage that is also the last");
+    dftR<R, S, Z>(a);
+  } else {
+    static_assert(Z == 0, "zero inputs in the first stage only");
+    static_assert(R == 2 || R == 4 || R == 8, "folded twiddles for radix 2, 4 and 8");
+    if constexpr (R == 2) dft2_folded<S, O>(a, T, k, L);
+    if constexpr (R == 4) dft4_folded<S, O>(a, T, k, L);
+    if constexpr (R == 8) dft8_folded<S, O>(a, T, k, L);
+  }
+}
+
+// Runs the butterfly for the warp's mask w, one of C, C|A, C|B, C|A|B of
+// GapMask G (w is warp-uniform, so the branches do not diverge); IN: w
+// masks inputs (Z), else outputs (O).
+template <int R, int S, int L, bool IN, typename G>
+__device__ __forceinline__ void masked_butterfly(double2* a, const double* T, int k, int w) {
+  constexpr int C = G::C, A = G::A, B = G::B;
+  if constexpr (A == 0) {
+    stage_butterfly<R, S, L, IN ? C : 0, IN ? 0 : C>(a, T, k);
+  } else if constexpr (B == 0) {
+    if (w & A) stage_butterfly<R, S, L, IN ? C | A : 0, IN ? 0 : C | A>(a, T, k);
+    else stage_butterfly<R, S, L, IN ? C : 0, IN ? 0 : C>(a, T, k);
+  } else {
+    if ((w & (A | B)) == (A | B)) stage_butterfly<R, S, L, IN ? C | A | B : 0, IN ? 0 : C | A | B>(a, T, k);
+    else if (w & A) stage_butterfly<R, S, L, IN ? C | A : 0, IN ? 0 : C | A>(a, T, k);
+    else if (w & B) stage_butterfly<R, S, L, IN ? C | B : 0, IN ? 0 : C | B>(a, T, k);
+    else stage_butterfly<R, S, L, IN ? C : 0, IN ? 0 : C>(a, T, k);
+  }
+}
+
+// No output pair of a folded butterfly (its two fma_pair_o halves) may be
+// masked whole: the flop count of band_transform_flops assumes that every
+// masked output saves its own two FMAs and nothing else.
+// (pairs: radix 2 (0, 1); radix 4 (0, 2), (1, 3); radix 8 (m, m + 4)).
+__host__ __device__ constexpr bool no_whole_pair(int r, int o) {
+  if (r == 2) return (o & 3) != 3;
+  if (r == 4) return (o & 5) != 5 && (o & 10) != 10;
+  if (r == 8) return (o & 0x11) != 0x11 && (o & 0x44) != 0x44 && (o & 0x22) != 0x22 && (o & 0x88) != 0x88;
+  return o == 0;
 }
 
 // One in-place Stockham stage with folded twiddles (T: this stage's table).
-template <int N, int V, int R, int S, int F, int L>
+// KIN >= 0: the input is band-limited to KIN (first stage skips the gap);
+// KOUT >= 0: only the band KOUT of the output is needed (last stage).
+template <int N, int V, int R, int S, int F, int L, int KIN, int KOUT>
 __device__ __forceinline__ void stockham_stage_folded(double2* buf, const double* __restrict__ T) {
   constexpr int NB = N / R, Th = PlanInfo<N, V>::THREADS, TOT = F * NB, J = (TOT + Th - 1) / Th;
+  constexpr bool FIRST = L == 1, LAST = L * R == N;
+  using GI = GapMask<N, R, FIRST ? KIN : -1>;
+  using GO = GapMask<N, R, LAST ? KOUT : -1>;
+  static_assert(no_whole_pair(R, GO::C | GO::A | GO::B), "a whole output pair in the gap");
   double2 a[J][R];
-  int base[J], dst[J];
+  int base[J], dst[J], om[J];
 #pragma unroll
   for (int jb = 0; jb < J; ++jb) {
     const int u = threadIdx.x + jb * Th;
     base[jb] = 0;
     dst[jb] = 0;
+    om[jb] = 0;
     if (TOT % Th == 0 || u < TOT) {
       const int f = u / NB;
       const int i = u - f * NB;
       const int k = i & (L - 1);
       base[jb] = f * N;
+      const int zm = GI::warp(i);
 #pragma unroll
-      for (int m = 0; m < R; ++m) a[jb][m] = buf[base[jb] + i + m * NB];
-      if constexpr (L == 1) {
-        dftR<R, S>(a[jb]);
+      for (int m = 0; m < R; ++m)
+        if (!((zm >> m) & 1)) a[jb][m] = buf[base[jb] + i + m * NB];
+      if constexpr (FIRST) {
+        masked_butterfly<R, S, L, true, GI>(a[jb], T, k, zm);
       } else {
-        static_assert(R == 2 || R == 4 || R == 8, "folded twiddles for radix 2, 4 and 8");
-        if constexpr (R == 2) dft2_folded<S>(a[jb], T, k, L);
-        if constexpr (R == 4) dft4_folded<S>(a[jb], T, k, L);
-        if constexpr (R == 8) dft8_folded<S>(a[jb], T, k, L);
+        om[jb] = GO::warp(i);
+        masked_butterfly<R, S, L, false, GO>(a[jb], T, k, om[jb]);
       }
       dst[jb] = (i - k) * R + k;
     }
@@ -381,29 +549,71 @@ __device__ __forceinline__ void stockham_stage_folded(double2* buf, const double
     const int u = threadIdx.x + jb * Th;
     if (TOT % Th == 0 || u < TOT) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) buf[base[jb] + dst[jb] + m * L] = a[jb][m];
+      for (int m = 0; m < R; ++m)
+        if (!((om[jb] >> m) & 1)) buf[base[jb] + dst[jb] + m * L] = a[jb][m];
     }
   }
   __syncthreads();
 }
 
-template <int N, int V, int S, int F, int L>
+template <int N, int V, int S, int F, int L, int KIN, int KOUT>
 __device__ __forceinline__ void run_stages_folded(double2*, const double*, Radices<>) {}
 
-template <int N, int V, int S, int F, int L, int R, int... Rs>
+template <int N, int V, int S, int F, int L, int KIN, int KOUT, int R, int... Rs>
 __device__ __forceinline__ void run_stages_folded(double2* buf, const double* T, Radices<R, Rs...>) {
-  stockham_stage_folded<N, V, R, S, F, L>(buf, T);
-  run_stages_folded<N, V, S, F, L * R>(buf, T + (L > 1 ? FoldSlots<R>::value * L : 0), Radices<Rs...>{});
+  stockham_stage_folded<N, V, R, S, F, L, KIN, KOUT>(buf, T);
+  run_stages_folded<N, V, S, F, L * R, KIN, KOUT>(buf, T + (L > 1 ? FoldSlots<R>::value * L : 0), Radices<Rs...>{});
 }
 
 // Transform, in place, F (1 or 2) sequences of N points stored back to back
 // in buf, with the folded table of Plan<N, V>::two (both lists of a plan
 // are the same radices) in shared memory.  Same contract as fft_batch, on a
-// CTA of PlanInfo<N, V>::THREADS threads.
-template <int N, int V, int S, int F>
+// CTA of PlanInfo<N, V>::THREADS threads.  KIN >= 0: every sequence is zero
+// in the gap KIN < q < N - KIN (the gap must hold zeros: warps that straddle
+// it still read it).  KOUT >= 0: the caller reads the result only at
+// q <= KOUT and q >= N - KOUT; the gap positions are left undefined.
+template <int N, int V, int S, int F, int KIN = -1, int KOUT = -1>
 __device__ __forceinline__ void fft_folded(double2* buf, const double* T) {
   static_assert(F == 1 || F == 2, "batches of one or two transforms");
-  run_stages_folded<N, V, S, F, 1>(buf, T, typename Plan<N, V>::two{});
+  run_stages_folded<N, V, S, F, 1, KIN, KOUT>(buf, T, typename Plan<N, V>::two{});
+}
+
+// Host side: flops of one band-limited transform of N points under Plan<N,
+// V> as the pass kernels run it: the nominal 5 N log2 N less the operations
+// the gap tests skip (a real addition or multiplication counts one, an FMA
+// two).  Inverse: the zero inputs of the first stage; forward: the unformed
+// outputs of the last (two FMAs each).
+template <typename P> struct FirstRadix;
+template <int R, int... Rs> struct FirstRadix<Radices<R, Rs...>> { static constexpr int value = R; };
+template <typename P> struct LastRadix;
+template <int R> struct LastRadix<Radices<R>> { static constexpr int value = R; };
+template <int R, int R2, int... Rs> struct LastRadix<Radices<R, R2, Rs...>> {
+  static constexpr int value = LastRadix<Radices<R2, Rs...>>::value;
+};
+
+// flops a zero mask z saves in the untwiddled r-point DFT (dft2/4/8/16):
+// every add_z / sub_z with a known-zero operand saves one complex addition
+constexpr int zero_savings(int r, int z) {
+  if (r == 2) return (z & 3) ? 4 : 0;
+  if (r == 4) {
+    const bool z0 = z & 1, z1 = (z >> 1) & 1, z2 = (z >> 2) & 1, z3 = (z >> 3) & 1;
+    return ((z0 || z2) ? 4 : 0) + ((z1 || z3) ? 4 : 0) + (((z0 && z2) || (z1 && z3)) ? 8 : 0);
+  }
+  return zero_savings(r / 2, even_bits(z, r)) + zero_savings(r / 2, odd_bits(z, r));
+}
+
+template <int N, int V, int KB>
+inline double band_transform_flops(bool inverse) {
+  using P = typename Plan<N, V>::two;
+  double saved = 0.0;
+  if (inverse) {
+    constexpr int R = FirstRadix<P>::value;
+    for (int i = 0; i < N / R; ++i) saved += zero_savings(R, GapMask<N, R, KB>::warp(i));
+  } else {
+    constexpr int R = LastRadix<P>::value;
+    for (int i = 0; i < N / R; ++i) saved += 4 * popcount_c(GapMask<N, R, KB>::warp(i));
+  }
+  return 5.0 * N * std::log2((double)N) - saved;
 }
 
 // Host side: fill the folded table of Plan<N, V>::two (FoldInfo<N, V>::DOUBLES

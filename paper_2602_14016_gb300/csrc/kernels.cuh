@@ -30,6 +30,10 @@
 // mirrors this with the transposed operators.  Every transform is an FP64
 // shared-memory FFT from fft.cuh; the 1/N^2 of the inverse 2D transform is
 // applied once, to the spectral coefficients before the column transform.
+// Every inverse transform here reads a sequence that is zero in the gap
+// K < q < N - K, and every forward transform is read back only on the band
+// q <= K, q >= N - K: the transforms are called band-limited (fft_folded
+// with KIN / KOUT = K) and skip that work where whole warps allow.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_r2c_rows(Dev d, const do
   #pragma unroll
   for (int x = threadIdx.x; x < N; x += G::THREADS) a[x] = make_double2(r0[x], r0[N + x]);
   __syncthreads();
-  fft_folded<N, V, -1, 1>(a, T);
+  fft_folded<N, V, -1, 1, -1, G::K>(a, T);
   double2* M = d.Mn + ((size_t)bm * 2 * N + y0) * G::Kc;
   #pragma unroll
   for (int kx = threadIdx.x; kx < G::Kc; kx += G::THREADS) {
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_c2r_rows(Dev d, double* 
   const double2* M = d.Mn + ((size_t)bm * 2 * N + y0) * G::Kc;
   pack_rows<N, G::THREADS>(a, M, M + G::Kc);
   __syncthreads();
-  fft_folded<N, V, +1, 1>(a, T);
+  fft_folded<N, V, +1, 1, G::K>(a, T);
   double* r0 = out + ((size_t)bm * N + y0) * N;
   #pragma unroll
   for (int x = threadIdx.x; x < N; x += G::THREADS) {
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_spec_to_mixed(Dev d, con
     a[q] = v;
   }
   __syncthreads();
-  fft_folded<N, V, +1, 1>(a, T);
+  fft_folded<N, V, +1, 1, G::K>(a, T);
   double2* M = d.Mn + (size_t)bm * 2 * N * G::Kc + kx;
   #pragma unroll
   for (int y = threadIdx.x; y < N; y += G::THREADS) M[(size_t)y * G::Kc] = a[y];
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_ctrl_cols(Dev d, int fla
   const double2* M = d.Mn + (size_t)bm * 2 * N * G::Kc + kx;
   load_column<N, G::THREADS, 1>(a, M);
   __syncthreads();
-  fft_folded<N, V, -1, 1>(a, T);
+  fft_folded<N, V, -1, 1, -1, G::K>(a, T);
   // each retained position is read and rewritten by one thread only
   #pragma unroll
   for (int rr = threadIdx.x; rr < G::Kr; rr += G::THREADS) {
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_ctrl_cols(Dev d, int fla
   if (flags & F_NO_NEXT) return;
   zero_outside<N>(a, 2);
   __syncthreads();
-  fft_folded<N, V, +1, 2>(a, T);
+  fft_folded<N, V, +1, 2, G::K>(a, T);
   store_mixed2<N, V>(d, a, bm, kx);
 }
 
@@ -470,7 +474,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_state_cols(Dev d) {
     put_stage_columns<N>(a, ky & (N - 1), d.symF[kx * G::Kr + rr], w);
   }
   __syncthreads();
-  fft_folded<N, V, +1, 2>(a, T);
+  fft_folded<N, V, +1, 2, G::K>(a, T);
   store_mixed2<N, V>(d, a, bm, kx);
 }
 
@@ -493,7 +497,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_rows(Dev d, int n, i
   load_fold<N, V>(T, d.fold);
   pack_field_pairs<N, V>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
   __syncthreads();
-  fft_folded<N, V, +1, 2>(a, T);
+  fft_folded<N, V, +1, 2, G::K>(a, T);
   const int P = mw.P, st = N / P;
   const int slot = (flags & (F_OBS | F_OBS_ONLY)) ? obs_slot(d, n - mw.start) : -1;
   double* trj = (flags & F_STORE)
@@ -527,7 +531,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_rows(Dev d, int n, i
   }
   if (flags & F_OBS_ONLY) return;
   __syncthreads();
-  fft_folded<N, V, -1, 2>(a, T);
+  fft_folded<N, V, -1, 2, -1, G::K>(a, T);
   unpack_field_rows<N, V>(a, d.Mn + (size_t)bm * 2 * N * G::Kc, y0);
 }
 
@@ -570,7 +574,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_cols(Dev d, int n, i
     for (int t = 0; t < MT; ++t) load_inputs(t);
   }
   __syncthreads();
-  fft_folded<N, V, -1, 2>(a, T);
+  fft_folded<N, V, -1, 2, -1, G::K>(a, T);
   const double dt = d.dt;
   const double fval = -d.amp * d.nf * (double)N * N / 2.0;
   // each retained position is read and rewritten (both sequences) by one
@@ -609,7 +613,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_cols(Dev d, int n, i
   if (flags & F_NO_NEXT) return;
   zero_outside<N>(a, 2);
   __syncthreads();
-  fft_folded<N, V, +1, 2>(a, T);
+  fft_folded<N, V, +1, 2, G::K>(a, T);
   store_mixed2<N, V>(d, a, bm, kx);
 }
 
@@ -721,7 +725,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_init(Dev d, int mode
     put_adjoint_columns<N>(a, ky & (N - 1), d.symA[kx * G::Kr + rr], kb);
   }
   __syncthreads();
-  fft_folded<N, V, +1, 2>(a, T);
+  fft_folded<N, V, +1, 2, G::K>(a, T);
   store_mixed2<N, V>(d, a, bm, kx);
 }
 
@@ -740,7 +744,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_rows(Dev d, int n, i
   load_fold<N, V>(T, d.fold);
   pack_field_pairs<N, V>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
   __syncthreads();
-  fft_folded<N, V, +1, 2>(a, T);
+  fft_folded<N, V, +1, 2, G::K>(a, T);
   const double* trj = d.traj + (((size_t)bm * d.traj_steps + (n - d.seg0)) * 4 + (stage - 1)) * 2 * (size_t)N * N;
   // one thread per column x reads (a, b) of both rows, then writes
   // rho_u and rho_v of both rows at x
@@ -759,7 +763,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_rows(Dev d, int n, i
     a[N + x] = make_double2(rv[0], rv[1]);
   }
   __syncthreads();
-  fft_folded<N, V, -1, 2>(a, T);
+  fft_folded<N, V, -1, 2, -1, G::K>(a, T);
   unpack_field_rows<N, V>(a, d.Mn + (size_t)bm * 2 * N * G::Kc, y0);
 }
 
@@ -803,7 +807,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_cols(Dev d, int n, i
   const int slot = (flags & F_SRC) ? obs_slot(d, n - mw.start) : -1;
   if (slot >= 0) probe_row_sums(d, bm, mw.P, slot, kx, Tu, Tv);
   __syncthreads();
-  fft_folded<N, V, -1, 2>(a, T);
+  fft_folded<N, V, -1, 2, -1, G::K>(a, T);
   const double dt = d.dt;
   // each retained position is read and rewritten (both sequences) by one
   // thread only
@@ -845,7 +849,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_cols(Dev d, int n, i
   if (stage == 1 && n == mw.start) return;  // the member's first step: lambda_0 stays in LamBar
   zero_outside<N>(a, 2);
   __syncthreads();
-  fft_folded<N, V, +1, 2>(a, T);
+  fft_folded<N, V, +1, 2, G::K>(a, T);
   store_mixed2<N, V>(d, a, bm, kx);
 }
 

@@ -12,6 +12,8 @@ struct Ops {
   int variant;                      // plan variant (fft.cuh)
   int threads;                      // CTA width of the pass kernels
   int fold_doubles;                 // entries of the folded twiddle table
+  double flops_inverse;             // nominal flops of one band-limited inverse transform
+  double flops_forward;             // ... and forward transform (band_transform_flops)
   void (*fold_table)(double* out);  // fills it on the host
   cudaError_t (*setup)();
   void (*r2c_rows)(const Dev&, const double* in, cudaStream_t);

@@ -15,6 +15,8 @@ Ops make_ops() {
   o.variant = V;
   o.threads = G::THREADS;
   o.fold_doubles = FoldInfo<N, V>::DOUBLES;
+  o.flops_inverse = band_transform_flops<N, V, G::K>(true);
+  o.flops_forward = band_transform_flops<N, V, G::K>(false);
   o.fold_table = [](double* out) { fold_table<N, V>(out); };
   o.setup = []() -> cudaError_t {
     const int s = (int)G::SMEM;

@@ -43,6 +43,15 @@ extern "C" int da_plan_count(int n) { return da::ops_for(n) ? da::plan_count(n) 
 
 extern "C" int da_get_plan(const da_ctx* c) { return c ? c->ops->variant : -1; }
 
+extern "C" da_status da_plan_flops(int n, int variant, double* inverse, double* forward) {
+  const Ops* o = da::ops_for(n, variant);
+  if (!o) return fail(nullptr, DA_EINVAL, "unsupported size or plan variant (da_plan_count)");
+  if (!inverse || !forward) return fail(nullptr, DA_EINVAL, "inverse and forward must not be NULL");
+  *inverse = o->flops_inverse;
+  *forward = o->flops_forward;
+  return DA_OK;
+}
+
 extern "C" da_status da_set_plan(da_ctx* c, int variant) {
   if (!c) return fail(c, DA_EINVAL, "ctx must not be NULL");
   // the folded table and the launchers change under any work in flight
