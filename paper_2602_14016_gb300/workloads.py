@@ -192,13 +192,20 @@ def autograd_check(api, torch, n=512, nsteps=4000, dt=1e-3, nu=1 / 200, nf=4, ck
     _, m = ctx.forward(s_truth)
     guess = torch.from_numpy(first_guess_from_probes(truth.cpu().numpy()[0], n, px)[None]).cuda()
     s0 = ctx.control_from_omega(guess)
-    s = s0.clone().requires_grad_(True)
-    t0 = time.perf_counter()
-    obs, _ = ag.solve(s, ctx)
-    L = ag.misfit(obs, m).sum()
-    L.backward()
-    torch.cuda.synchronize()
-    t_grad = time.perf_counter() - t0
+    # the first gradient of a process also pays one-time set-up: measured on
+    # GB300, its autograd backward took about 5 s more than later ones, while
+    # a first da_vjp called directly takes about 0.3 s more; the second
+    # gradient is the steady cost
+    t_grad = []
+    for _ in range(2):
+        s = s0.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        obs, _ = ag.solve(s, ctx)
+        L = ag.misfit(obs, m).sum()
+        L.backward()
+        torch.cuda.synchronize()
+        t_grad.append(time.perf_counter() - t0)
     g = s.grad.detach()
     errs = np.zeros((len(eps), directions))
     for k in range(directions):
@@ -211,7 +218,8 @@ def autograd_check(api, torch, n=512, nsteps=4000, dt=1e-3, nu=1 / 200, nf=4, ck
             errs[i, k] = abs((Lp - Lm) / (2 * e) - gd) / max(abs(gd), 1e-300)
     best = errs.min(axis=0)
     out = {"n": n, "nsteps": nsteps, "ckpt_every": ckpt_every, "device_bytes": ctx.device_bytes,
-           "full_storage_bytes": nsteps * 8 * n * n * 8, "loss": float(L.detach()), "grad_seconds": t_grad,
+           "full_storage_bytes": nsteps * 8 * n * n * 8, "loss": float(L.detach()), "grad_seconds": t_grad[1],
+           "grad_seconds_first_call": t_grad[0],
            "directions": directions, "eps": list(eps),
            "fd_rel_err_median_per_eps": [float(np.median(r)) for r in errs],
            "fd_rel_err_best_eps_median": float(np.median(best)), "fd_rel_err_best_eps_max": float(best.max())}
