@@ -192,9 +192,10 @@ def autograd_check(api, torch, n=512, nsteps=4000, dt=1e-3, nu=1 / 200, nf=4, ck
     _, m = ctx.forward(s_truth)
     guess = torch.from_numpy(first_guess_from_probes(truth.cpu().numpy()[0], n, px)[None]).cuda()
     s0 = ctx.control_from_omega(guess)
-    # the first gradient of a process also pays one-time set-up: measured on
-    # GB300, its autograd backward took about 5 s more than later ones, while
-    # a first da_vjp called directly takes about 0.3 s more; the second
+    # the first gradient of a process can also pay one-time set-up: on a
+    # fresh GB300 machine the first autograd backward took about 5 s more
+    # than later ones (not when an earlier process had run there), while a
+    # first da_vjp called directly takes about 0.3 s more; the second
     # gradient is the steady cost
     t_grad = []
     for _ in range(2):
