@@ -558,7 +558,7 @@ def run_workload(args):
         fwd.close()
         w_guess = workloads.first_guess_from_probes(w_truth, n, 8)
         out = workloads.assimilation_run(api, torch, cfg, obs.cpu().numpy(), w_guess[None], w_truth[None],
-                                         args.assim_iters)
+                                         args.assim_iters, plan=args.plan)
         line.update({"metric": "plain-method assimilation: first evaluation and L-BFGS iterations", **out,
                      "config": {"grid": n, "nsteps": nsteps, "dt": 5e-3, "nu": 1e-3, "probes": "8x8 every 10",
                                 "kernel": "exp_abs:0.5", "iters": args.assim_iters}})
@@ -643,6 +643,8 @@ def main():
     ap.add_argument("--roofline-evals", type=int, default=1)
     ap.add_argument("--no-graphs", dest="graphs", action="store_false")
     ap.add_argument("--tune-steps", type=int, default=8, help="RK steps per plan variant in the autotuner (0: off)")
+    ap.add_argument("--plan", type=int, default=None,
+                    help="plain: a fixed FFT plan variant instead of the autotuner's choice (e.g. under a profiler)")
     ap.add_argument("--probe-iters", type=int, default=100000, help="fp64peak: loop rounds per thread")
     ap.add_argument("--assim-iters", type=int, default=None,
                     help="plain / sweep-assim: L-BFGS iterations (defaults 10 and 100)")

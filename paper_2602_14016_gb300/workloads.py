@@ -71,13 +71,16 @@ def initial_velocity_error(w_est: np.ndarray, w_true: np.ndarray) -> float:
     return float(np.sqrt(num / den))
 
 
-def assimilation_run(api, torch, cfg, m, w_guess, w_truth, iters, graphs=True, tune_steps=4):
+def assimilation_run(api, torch, cfg, m, w_guess, w_truth, iters, graphs=True, tune_steps=4, plan=None):
     """One cost-and-gradient evaluation at the first guess, then `iters` L-BFGS
     iterations of every member (da_assimilate).  m: observations [B, nt, P^2, 2];
-    w_guess, w_truth: vorticity half spectra [B or 1, n, nh].  Returns timings,
+    w_guess, w_truth: vorticity half spectra [B or 1, n, nh].  plan: a fixed
+    FFT plan variant instead of the autotuner's choice.  Returns timings,
     J histories, statuses and initial-velocity errors before and after."""
     ctx = api.Context(cfg)
-    if tune_steps > 0:
+    if plan is not None:
+        ctx.set_plan(plan)
+    elif tune_steps > 0:
         ctx.autotune(tune_steps)
     if graphs:
         ctx.set_graphs(True)
