@@ -11,11 +11,25 @@ zero-aware DFTs (an even/odd split down to 4-point DFTs, whose additions
 with a known-zero operand cost nothing) and of the folded last-stage
 butterflies (two FMAs per output).
 """
+import ctypes
 import math
+import os
+import shutil
 
 import pytest
 
 from paper_2602_14016_gb300 import _native as NN
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_14016_gb300 import build
+
+    if shutil.which("nvcc") or os.path.exists("/usr/local/cuda/bin/nvcc"):
+        build.build()
+    if not os.path.exists(NN.LIB_PATH):
+        pytest.fail("libda_gb300.so is not built and nvcc is unavailable")
+    return NN.load()
 
 # radix lists and CTA widths of the plan variants
 PLANS = {16: [(4, 4)], 32: [(4, 8), (2,) * 5], 64: [(4, 4, 4), (8, 8), (2,) * 6],
@@ -67,10 +81,7 @@ def skipped_flops(n, radices):
 
 
 @pytest.mark.parametrize("n", sorted(PLANS))
-def test_plan_flops_match_the_gap_rule(n):
-    import ctypes
-
-    lib = NN.load()
+def test_plan_flops_match_the_gap_rule(lib, n):
     assert lib.da_plan_count(n) == len(PLANS[n])
     nominal = 5.0 * n * math.log2(n)
     for v, radices in enumerate(PLANS[n]):
@@ -83,25 +94,19 @@ def test_plan_flops_match_the_gap_rule(n):
         assert 0.9 * nominal < inv.value <= nominal and 0.9 * nominal < fwd.value <= nominal
 
 
-def test_headline_grid_counts():
+def test_headline_grid_counts(lib):
     """At 256 (radix 4 x 4 x 4 x 4): per sequence, warp 0 (butterflies 0-31)
     has input/output 2 (positions 128-159) in the gap and warp 1 has input
     or output 1 (positions 96-127): 64 butterflies x 2 complex additions
     (4 flops) skipped in an inverse transform, 64 outputs x 2 FMAs (4 flops)
     in a forward one."""
-    import ctypes
-
-    lib = NN.load()
     inv, fwd = ctypes.c_double(), ctypes.c_double()
     assert lib.da_plan_flops(256, 0, ctypes.byref(inv), ctypes.byref(fwd)) == NN.DA_OK
     assert inv.value == 5 * 256 * 8 - 64 * 4 and fwd.value == 5 * 256 * 8 - 64 * 4
     assert gap_masks(256, 4)[:32] == [4] * 32 and gap_masks(256, 4)[32:] == [2] * 32
 
 
-def test_plan_flops_rejects():
-    import ctypes
-
-    lib = NN.load()
+def test_plan_flops_rejects(lib):
     x = ctypes.c_double()
     assert lib.da_plan_flops(100, 0, ctypes.byref(x), ctypes.byref(x)) == NN.DA_EINVAL
     assert lib.da_plan_flops(256, 3, ctypes.byref(x), ctypes.byref(x)) == NN.DA_EINVAL
