@@ -270,7 +270,10 @@ def run_gpu(args):
     # FFT plan: the autotuner times each variant on this batch (outside the
     # timed region) and keeps the fastest
     tune = {"chosen": ctx.plan, "ms_per_step": None}
-    if args.tune_steps > 0:
+    if args.plan is not None:
+        ctx.set_plan(args.plan)
+        tune["chosen"] = ctx.plan
+    elif args.tune_steps > 0:
         tune["chosen"], tune["ms_per_step"] = ctx.autotune(args.tune_steps)
     ctx.set_observations(torch.from_numpy(m).to(device))
     s = ctx.control_from_omega(torch.from_numpy(w_guess).to(device))
@@ -644,7 +647,8 @@ def main():
     ap.add_argument("--no-graphs", dest="graphs", action="store_false")
     ap.add_argument("--tune-steps", type=int, default=8, help="RK steps per plan variant in the autotuner (0: off)")
     ap.add_argument("--plan", type=int, default=None,
-                    help="plain: a fixed FFT plan variant instead of the autotuner's choice (e.g. under a profiler)")
+                    help="sweep, plain: a fixed FFT plan variant instead of the autotuner's choice "
+                         "(e.g. under a profiler)")
     ap.add_argument("--probe-iters", type=int, default=100000, help="fp64peak: loop rounds per thread")
     ap.add_argument("--assim-iters", type=int, default=None,
                     help="plain / sweep-assim: L-BFGS iterations (defaults 10 and 100)")
