@@ -6,8 +6,13 @@
 //                    r -> ky = r (r <= K) or r - Kr; K = floor((N-1)/3),
 //                    Kc = K+1, Kr = 2K+1.  A column pass reads and writes one
 //                    contiguous column.
-//   mixed fields     [2][N][Kc] complex: physical y, spectral kx (the
-//                    transform along y of a compact column), two fields.
+//   mixed fields     physical y, spectral kx (kx = 0..K), two fields: the
+//                    column-pass output Mx row-major [2][N][Kc] (a row
+//                    pass reads whole rows), the row-pass output Mn
+//                    column-major [Kc][2][N] (a column pass reads its
+//                    column of both fields as one contiguous block; a row
+//                    pass writes rows y0, y0+1 of a column as one 32-byte
+//                    pair).
 //   stage fields     [nsteps][4 stages][2 fields][N][N] double: u, v of
 //                    every RK stage state, written by the forward row pass
 //                    and read back by the adjoint row pass.
@@ -93,7 +98,7 @@ struct Dev {
   size_t obs_stride;                         // doubles from one member's obs, mobs, res to the next
   double2 *W, *Acc, *Y, *KB, *LamBar, *Sum;  // compact [B][Kc][Kr] (cidx)
   double2* Mx;                               // mixed [B][2][N][Kc]: column-pass output
-  double2* Mn;                               // mixed [B][2][N][Kc]: row-pass output
+  double2* Mn;                               // mixed [B][Kc][2][N]: row-pass output
   double* traj;                              // [B][traj_steps][4][2][N][N]
   int traj_steps;                            // steps the stage-field store holds
   int seg0;                                  // step stored in slot 0 of the store
@@ -161,26 +166,12 @@ __device__ __forceinline__ int obs_slot(const Dev& d, int k) {
 
 // Full-length sequence whose inverse transform is a + i b, for two real rows
 // a, b given by their mixed half spectra A, B (kx = 0..K): Z(kx) = A + iB,
-// Z(-kx) = conj(A) + i conj(B); the DC bin keeps real parts only.
-template <int N, int V = 0>
-__device__ __forceinline__ double2 pack_pair(const double2* __restrict__ A, const double2* __restrict__ Bv, int kx) {
-  constexpr int K = Geo<N, V>::K;
-  if (kx == 0) return make_double2(A[0].x, Bv[0].x);
-  if (kx <= K) {
-    const double2 p = A[kx], q = Bv[kx];
-    return make_double2(p.x - q.y, p.y + q.x);
-  }
-  if (kx >= N - K) {
-    const double2 p = A[N - kx], q = Bv[N - kx];
-    return make_double2(p.x + q.y, q.x - p.y);
-  }
-  return make_double2(0.0, 0.0);
-}
-
-// Same packing for a whole sequence: every coefficient is loaded once and
-// written to kx and -kx; the gap K < kx < N-K is zeroed.  Loops run over
-// compile-time trip counts so that a thread's loads are issued together.
-template <int N, int T>
+// Z(-kx) = conj(A) + i conj(B); the DC bin keeps real parts only.  Every
+// coefficient is loaded once and written to kx and -kx; the gap
+// K < kx < N-K is zeroed.  Coefficient kx of A and Bv is at [kx * STRIDE].
+// Loops run over compile-time trip counts so that a thread's loads are
+// issued together.
+template <int N, int T, int STRIDE = 1>
 __device__ __forceinline__ void pack_rows(double2* seq, const double2* __restrict__ A, const double2* __restrict__ Bv) {
   constexpr int K = Geo<N>::K, GAP = N - 2 * K - 1;
 #pragma unroll
@@ -192,7 +183,7 @@ __device__ __forceinline__ void pack_rows(double2* seq, const double2* __restric
   for (int t = 0; t < (K + 1 + T - 1) / T; ++t) {
     const int kx = threadIdx.x + t * T;
     if (kx <= K) {
-      const double2 p = A[kx], q = Bv[kx];
+      const double2 p = A[(size_t)kx * STRIDE], q = Bv[(size_t)kx * STRIDE];
       if (kx == 0) {
         seq[0] = make_double2(p.x, q.x);
       } else {
@@ -242,13 +233,13 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_r2c_rows(Dev d, const do
   for (int x = threadIdx.x; x < N; x += G::THREADS) a[x] = make_double2(r0[x], r0[N + x]);
   __syncthreads();
   fft_folded<N, V, -1, 1, -1, G::K>(a, T);
-  double2* M = d.Mn + ((size_t)bm * 2 * N + y0) * G::Kc;
+  double2* M = d.Mn + (size_t)bm * G::Kc * 2 * N + y0;  // field 0, rows y0 and y0 + 1
   #pragma unroll
   for (int kx = threadIdx.x; kx < G::Kc; kx += G::THREADS) {
     double2 A, Bv;
     unpack_pair<N>(a, kx, A, Bv);
-    M[kx] = A;
-    M[G::Kc + kx] = Bv;
+    M[(size_t)kx * 2 * N] = A;
+    M[(size_t)kx * 2 * N + 1] = Bv;
   }
 }
 
@@ -262,8 +253,8 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_c2r_rows(Dev d, double* 
   double2* a = sm + FoldInfo<N, V>::PADDED / 2;
   const int bm = blockIdx.y, y0 = 2 * blockIdx.x;
   load_fold<N, V>(T, d.fold);
-  const double2* M = d.Mn + ((size_t)bm * 2 * N + y0) * G::Kc;
-  pack_rows<N, G::THREADS>(a, M, M + G::Kc);
+  const double2* M = d.Mn + (size_t)bm * G::Kc * 2 * N + y0;  // field 0, rows y0 and y0 + 1
+  pack_rows<N, G::THREADS, 2 * N>(a, M, M + 1);
   __syncthreads();
   fft_folded<N, V, +1, 1, G::K>(a, T);
   double* r0 = out + ((size_t)bm * N + y0) * N;
@@ -304,9 +295,9 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_spec_to_mixed(Dev d, con
   }
   __syncthreads();
   fft_folded<N, V, +1, 1, G::K>(a, T);
-  double2* M = d.Mn + (size_t)bm * 2 * N * G::Kc + kx;
+  double2* M = d.Mn + ((size_t)bm * G::Kc + kx) * 2 * N;  // field 0 of column kx
   #pragma unroll
-  for (int y = threadIdx.x; y < N; y += G::THREADS) M[(size_t)y * G::Kc] = a[y];
+  for (int y = threadIdx.x; y < N; y += G::THREADS) M[y] = a[y];
 }
 
 // Compact <-> half-spectrum copies.  grid (ceil(N*NH/256), B), block 256.
@@ -380,15 +371,15 @@ __device__ __forceinline__ void store_mixed2(const Dev& d, const double2* z, int
   }
 }
 
-// F whole columns (stride Kc, consecutive columns of F fields N*Kc apart)
-// into seq[f*N + y], with a compile-time trip count.
+// Column kx of the first F fields of the column-major Mn (M points at the
+// column: F * N contiguous entries, field-major) into seq[f*N + y], with a
+// compile-time trip count.
 template <int N, int T, int F>
 __device__ __forceinline__ void load_column(double2* seq, const double2* __restrict__ M) {
-  constexpr int Kc = Geo<N>::Kc;
 #pragma unroll
   for (int t = 0; t < (F * N + T - 1) / T; ++t) {
     const int u = threadIdx.x + t * T;
-    if (u < F * N) seq[u] = M[(size_t)u * Kc];
+    if (u < F * N) seq[u] = M[u];
   }
 }
 
@@ -405,7 +396,8 @@ __device__ __forceinline__ void pack_field_pairs(double2* a, const double2* __re
 
 // Forward transforms along x of rows y0, y0+1 of two real fields, packed as
 // seq f = (field f row y0) + i (field f row y0+1) -> twice the rows of both
-// fields of the mixed buffer O (kx <= K).
+// fields of the column-major mixed buffer O = Mn of the member (kx <= K):
+// entries (kx, f, y0) and (kx, f, y0 + 1) are adjacent, one 32-byte store pair.
 template <int N, int V = 0>
 __device__ __forceinline__ void unpack_field_rows(const double2* a, double2* __restrict__ O, int y0) {
   using G = Geo<N, V>;
@@ -416,8 +408,9 @@ __device__ __forceinline__ void unpack_field_rows(const double2* a, double2* __r
       const int f = u / G::Kc, kx = u - f * G::Kc;
       double2 A, Bv;
       unpack_pair2<N>(a + f * N, kx, A, Bv);
-      O[((size_t)f * N + y0) * G::Kc + kx] = A;
-      O[((size_t)f * N + y0 + 1) * G::Kc + kx] = Bv;
+      double2* o = O + ((size_t)kx * 2 + f) * N + y0;
+      o[0] = A;
+      o[1] = Bv;
     }
   }
 }
@@ -433,8 +426,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_ctrl_cols(Dev d, int fla
   double2* a = sm + FoldInfo<N, V>::PADDED / 2;
   const int kx = blockIdx.x, bm = blockIdx.y;
   load_fold<N, V>(T, d.fold);
-  const double2* M = d.Mn + (size_t)bm * 2 * N * G::Kc + kx;
-  load_column<N, G::THREADS, 1>(a, M);
+  load_column<N, G::THREADS, 1>(a, d.Mn + ((size_t)bm * G::Kc + kx) * 2 * N);
   __syncthreads();
   fft_folded<N, V, -1, 1, -1, G::K>(a, T);
   // each retained position is read and rewritten by one thread only
@@ -532,7 +524,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_rows(Dev d, int n, i
   if (flags & F_OBS_ONLY) return;
   __syncthreads();
   fft_folded<N, V, -1, 2, -1, G::K>(a, T);
-  unpack_field_rows<N, V>(a, d.Mn + (size_t)bm * 2 * N * G::Kc, y0);
+  unpack_field_rows<N, V>(a, d.Mn + (size_t)bm * G::Kc * 2 * N, y0);
 }
 
 // Column pass of stage `stage`: the advection term
@@ -550,7 +542,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_cols(Dev d, int n, i
   const MemberWindow mw = member_window(d, bm);
   if (n < mw.start) return;
   load_fold<N, V>(T, d.fold);
-  load_column<N, G::THREADS, 2>(a, d.Mn + (size_t)bm * 2 * N * G::Kc + kx);
+  load_column<N, G::THREADS, 2>(a, d.Mn + ((size_t)bm * G::Kc + kx) * 2 * N);
   // the epilogue's inputs for this thread's modes; where registers allow
   // (G::PREFETCH), loaded now so that their latency hides behind the
   // column transforms
@@ -764,7 +756,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_rows(Dev d, int n, i
   }
   __syncthreads();
   fft_folded<N, V, -1, 2, -1, G::K>(a, T);
-  unpack_field_rows<N, V>(a, d.Mn + (size_t)bm * 2 * N * G::Kc, y0);
+  unpack_field_rows<N, V>(a, d.Mn + (size_t)bm * G::Kc * 2 * N, y0);
 }
 
 // Adjoint column pass of stage `stage` of step n:
@@ -782,7 +774,7 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_cols(Dev d, int n, i
   const MemberWindow mw = member_window(d, bm);
   if (n < mw.start) return;
   load_fold<N, V>(T, d.fold);
-  load_column<N, G::THREADS, 2>(a, d.Mn + (size_t)bm * 2 * N * G::Kc + kx);
+  load_column<N, G::THREADS, 2>(a, d.Mn + ((size_t)bm * G::Kc + kx) * 2 * N);
   // the epilogue's inputs for this thread's modes (before the column
   // transforms where registers allow, as in k_fwd_cols)
   constexpr int MT = (G::Kr + G::THREADS - 1) / G::THREADS;
