@@ -598,17 +598,24 @@ def run_workload(args):
 
             free = torch.cuda.mem_get_info()[0]
             budget = int(0.6 * free)
-            # co-batched: one pool per grid size, `slots` member slots each, its
-            # share of the budget; checkpoints when full storage does not fit
-            pools = {}
-            for n in args.serve_grids:
-                share = budget // len(args.serve_grids)
+
+            def size_pools(grids, mem):
+                """One pool per grid size, `co_slots` member slots each: full
+                trajectory storage when every pool's fits in `mem`, else an
+                equal share each, checkpointed where full storage does not fit."""
                 nmax = args.serve_steps[1] // 10 * 10
-                ck = 0
-                if serve.CoBatchServer.pool_bytes(n, nmax, 32, 10, 0, args.co_slots) > share:
-                    ck = next((K for K in range(nmax, 0, -1)
-                               if serve.CoBatchServer.pool_bytes(n, nmax, 32, 10, K, args.co_slots) <= share), 1)
-                pools[n] = dict(slots=args.co_slots, nsteps=nmax, px=32, dt=dts[n], ckpt_every=ck)
+                full = {n: serve.CoBatchServer.pool_bytes(n, nmax, 32, 10, 0, args.co_slots) for n in grids}
+                out = {}
+                for n in grids:
+                    ck = 0
+                    if sum(full.values()) > mem and full[n] > mem // len(grids):
+                        ck = next((K for K in range(nmax, 0, -1)
+                                   if serve.CoBatchServer.pool_bytes(n, nmax, 32, 10, K, args.co_slots)
+                                   <= mem // len(grids)), 1)
+                    out[n] = dict(slots=args.co_slots, nsteps=nmax, px=32, dt=dts[n], ckpt_every=ck)
+                return out
+
+            pools = size_pools(args.serve_grids, budget)
             co = serve.CoBatchServer(pools, plan=None)
             out_co = co.run(fresh_jobs())
             co.close()
@@ -619,13 +626,15 @@ def run_workload(args):
                                 job_cap=int(budget / args.slots)).run(fresh_jobs())
             # hybrid: grids up to 256^2 co-batched in pools, larger ones as their own contexts
             small = [n for n in args.serve_grids if n <= 256]
-            hy = serve.HybridServer({n: pools[n] for n in small}, big_budget=budget // 2, big_slots=2,
-                                    plan=None)
+            big_budget = budget // 2
+            hy_pools = size_pools(small, budget - big_budget)
+            hy = serve.HybridServer(hy_pools, big_budget=big_budget, big_slots=2, plan=None)
             out_hy = hy.run(fresh_jobs())
             hy.close()
             torch.cuda.empty_cache()
             summary[str(rate)] = {"co_batched": out_co, "hybrid": out_hy, "stream_overlap": out,
-                                  "one_job_at_a_time": base, "pools": {str(n): p for n, p in pools.items()}}
+                                  "one_job_at_a_time": base, "pools": {str(n): p for n, p in pools.items()},
+                                  "hybrid_pools": {str(n): p for n, p in hy_pools.items()}}
         line.update({"metric": "served solves/s, p50/p99 latency", "rates": summary,
                      "config": {"jobs": args.serve_jobs, "slots": args.slots, "co_slots": args.co_slots,
                                 "grids": args.serve_grids,
