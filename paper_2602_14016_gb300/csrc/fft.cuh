@@ -565,6 +565,25 @@ __device__ __forceinline__ void run_stages_folded(double2* buf, const double* T,
   run_stages_folded<N, V, S, F, L * R, KIN, KOUT>(buf, T + (L > 1 ? FoldSlots<R>::value * L : 0), Radices<Rs...>{});
 }
 
+// First and last radix of a plan, the plan without its last stage, and
+// without its first.
+template <typename P> struct FirstRadix;
+template <int R, int... Rs> struct FirstRadix<Radices<R, Rs...>> { static constexpr int value = R; };
+template <typename P> struct LastRadix;
+template <int R> struct LastRadix<Radices<R>> { static constexpr int value = R; };
+template <int R, int R2, int... Rs> struct LastRadix<Radices<R, R2, Rs...>> {
+  static constexpr int value = LastRadix<Radices<R2, Rs...>>::value;
+};
+template <int R, typename P> struct Prepend;
+template <int R, int... Rs> struct Prepend<R, Radices<Rs...>> { using type = Radices<R, Rs...>; };
+template <typename P> struct InitRadices;
+template <int R> struct InitRadices<Radices<R>> { using type = Radices<>; };
+template <int R, int R2, int... Rs> struct InitRadices<Radices<R, R2, Rs...>> {
+  using type = typename Prepend<R, typename InitRadices<Radices<R2, Rs...>>::type>::type;
+};
+template <typename P> struct TailRadices;
+template <int R, int... Rs> struct TailRadices<Radices<R, Rs...>> { using type = Radices<Rs...>; };
+
 // Transform, in place, F (1 or 2) sequences of N points stored back to back
 // in buf, with the folded table of Plan<N, V>::two (both lists of a plan
 // are the same radices) in shared memory.  Same contract as fft_batch, on a
@@ -578,18 +597,74 @@ __device__ __forceinline__ void fft_folded(double2* buf, const double* T) {
   run_stages_folded<N, V, S, F, 1, KIN, KOUT>(buf, T, typename Plan<N, V>::two{});
 }
 
+// Whether an inverse transform, a pointwise map and a forward transform of the
+// same sequences can hand the data over in registers: when the plan's first
+// and last radix agree, the thread that forms outputs k + m N/R of the last
+// inverse stage is the thread that needs inputs i + m N/R (i = k) of the
+// first forward stage.
+template <int N, int V>
+struct Fusable {
+  using P = typename Plan<N, V>::two;
+  static constexpr bool value = FirstRadix<P>::value == LastRadix<P>::value;
+};
+
+// Inverse transform (S = +1, input band-limited to KIN), then op applied to
+// every output point, then forward transform (S = -1, output needed on the
+// band KOUT) of F sequences in buf: the last inverse stage, op and the first
+// forward stage run on registers, between one pair of barriers.  op(f, x, z)
+// gets sequence f, position x and the inverse transform's value there, and
+// returns the forward transform's input there.  Same contract as two
+// fft_folded calls with op applied in between; requires Fusable<N, V>.
+template <int N, int V, int F, int KIN, int KOUT, typename Op>
+__device__ __forceinline__ void fft_folded_turn(double2* buf, const double* T, Op op) {
+  using P = typename Plan<N, V>::two;
+  static_assert(Fusable<N, V>::value, "first and last radix must agree");
+  constexpr int R = LastRadix<P>::value, NB = N / R, L = N / R;
+  constexpr int Th = PlanInfo<N, V>::THREADS, TOT = F * NB, J = (TOT + Th - 1) / Th;
+  // inverse stages but the last
+  run_stages_folded<N, V, +1, F, 1, KIN, -1>(buf, T, typename InitRadices<P>::type{});
+  const double* Tl = T + FoldSize<1, typename InitRadices<P>::type>::value;
+  double2 a[J][R];
+  int base[J], ii[J];
+#pragma unroll
+  for (int jb = 0; jb < J; ++jb) {
+    const int u = threadIdx.x + jb * Th;
+    base[jb] = 0;
+    ii[jb] = 0;
+    if (TOT % Th == 0 || u < TOT) {
+      const int f = u / NB;
+      const int i = u - f * NB;
+      base[jb] = f * N;
+      ii[jb] = i;
+#pragma unroll
+      for (int m = 0; m < R; ++m) a[jb][m] = buf[base[jb] + i + m * NB];
+      stage_butterfly<R, +1, L, 0, 0>(a[jb], Tl, i);  // last inverse stage: class k = i
+    }
+  }
+  __syncthreads();  // every thread has read buf
+#pragma unroll
+  for (int jb = 0; jb < J; ++jb) {
+    const int u = threadIdx.x + jb * Th;
+    if (TOT % Th == 0 || u < TOT) {
+      const int f = u / NB;
+#pragma unroll
+      for (int m = 0; m < R; ++m) a[jb][m] = op(f, ii[jb] + m * L, a[jb][m]);
+      dftR<R, -1, 0>(a[jb]);  // first forward stage
+#pragma unroll
+      for (int m = 0; m < R; ++m) buf[base[jb] + ii[jb] * R + m] = a[jb][m];
+    }
+  }
+  __syncthreads();
+  // forward stages after the first (its table slots start at 0: the first
+  // stage has none)
+  run_stages_folded<N, V, -1, F, R, -1, KOUT>(buf, T, typename TailRadices<P>::type{});
+}
+
 // Host side: flops of one band-limited transform of N points under Plan<N,
 // V> as the pass kernels run it: the nominal 5 N log2 N less the operations
 // the gap tests skip (a real addition or multiplication counts one, an FMA
 // two).  Inverse: the zero inputs of the first stage; forward: the unformed
 // outputs of the last (two FMAs each).
-template <typename P> struct FirstRadix;
-template <int R, int... Rs> struct FirstRadix<Radices<R, Rs...>> { static constexpr int value = R; };
-template <typename P> struct LastRadix;
-template <int R> struct LastRadix<Radices<R>> { static constexpr int value = R; };
-template <int R, int R2, int... Rs> struct LastRadix<Radices<R, R2, Rs...>> {
-  static constexpr int value = LastRadix<Radices<R2, Rs...>>::value;
-};
 
 // flops a zero mask z saves in the untwiddled r-point DFT (dft2/4/8/16):
 // every add_z / sub_z with a known-zero operand saves one complex addition

@@ -10,9 +10,7 @@
 //                    column-pass output Mx row-major [2][N][Kc] (a row
 //                    pass reads whole rows), the row-pass output Mn
 //                    column-major [Kc][2][N] (a column pass reads its
-//                    column of both fields as one contiguous block; a row
-//                    pass writes rows y0, y0+1 of a column as one 32-byte
-//                    pair).
+//                    column of both fields as one contiguous block).
 //   stage fields     [nsteps][4 stages][2 fields][N][N] double: u, v of
 //                    every RK stage state, written by the forward row pass
 //                    and read back by the adjoint row pass.
@@ -28,7 +26,8 @@
 //
 // A forward RK stage is two kernels: a ROW pass (inverse transforms along x
 // of the packed mixed rows -> u, v; stage-field store; probe gather; the
-// products u v and v^2 - u^2; their forward transforms along x) and a COLUMN
+// products u v and v^2 - u^2; their forward transforms along x, handed over
+// in registers where the plan allows: fft_folded_turn) and a COLUMN
 // pass (forward transforms along y of the two products, the advection term,
 // RK epilogue with viscosity, forcing and the stage update, then the
 // inverse column transforms of the next stage's u and v).  The adjoint
@@ -394,23 +393,23 @@ __device__ __forceinline__ void pack_field_pairs(double2* a, const double2* __re
     pack_rows<N, Geo<N, V>::THREADS>(a + rr * N, M + (size_t)(y0 + rr) * Kc, M + ((size_t)N + y0 + rr) * Kc);
 }
 
-// Forward transforms along x of rows y0, y0+1 of two real fields, packed as
-// seq f = (field f row y0) + i (field f row y0+1) -> twice the rows of both
-// fields of the column-major mixed buffer O = Mn of the member (kx <= K):
-// entries (kx, f, y0) and (kx, f, y0 + 1) are adjacent, one 32-byte store pair.
+// Forward transforms along x of rows y0, y0+1, sequence rr packed as
+// (field 0 of row y0+rr) + i (field 1 of row y0+rr) -> twice the two fields
+// of both rows in the column-major mixed buffer O = Mn of the member
+// (kx <= K): entry (kx, f, y) at (kx * 2 + f) * N + y.
 template <int N, int V = 0>
-__device__ __forceinline__ void unpack_field_rows(const double2* a, double2* __restrict__ O, int y0) {
+__device__ __forceinline__ void unpack_row_pairs(const double2* a, double2* __restrict__ O, int y0) {
   using G = Geo<N, V>;
 #pragma unroll
   for (int t = 0; t < (2 * G::Kc + G::THREADS - 1) / G::THREADS; ++t) {
     const int u = threadIdx.x + t * G::THREADS;
     if (u < 2 * G::Kc) {
-      const int f = u / G::Kc, kx = u - f * G::Kc;
+      const int rr = u / G::Kc, kx = u - rr * G::Kc;
       double2 A, Bv;
-      unpack_pair2<N>(a + f * N, kx, A, Bv);
-      double2* o = O + ((size_t)kx * 2 + f) * N + y0;
+      unpack_pair2<N>(a + rr * N, kx, A, Bv);
+      double2* o = O + (size_t)kx * 2 * N + y0 + rr;
       o[0] = A;
-      o[1] = Bv;
+      o[N] = Bv;
     }
   }
 }
@@ -475,8 +474,9 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_state_cols(Dev d) {
 // ---------------------------------------------------------------------------
 
 // Row pass of stage `stage` (1..4) of step n: u, v of rows y0, y0+1; the
-// stage-field store and probe gather; the products u v and v^2 - u^2 and
-// their forward transforms along x into Mn.  grid (N/2, B).
+// stage-field store and probe gather; the products u v and v^2 - u^2 of
+// each row (packed as P + i Q) and their forward transforms along x into
+// Mn.  grid (N/2, B).
 template <int N, int V = 0>
 __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_rows(Dev d, int n, int stage, int flags) {
   using G = Geo<N, V>;
@@ -489,42 +489,47 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_fwd_rows(Dev d, int n, i
   load_fold<N, V>(T, d.fold);
   pack_field_pairs<N, V>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
   __syncthreads();
-  fft_folded<N, V, +1, 2, G::K>(a, T);
   const int P = mw.P, st = N / P;
   const int slot = (flags & (F_OBS | F_OBS_ONLY)) ? obs_slot(d, n - mw.start) : -1;
   double* trj = (flags & F_STORE)
                     ? d.traj + (((size_t)bm * d.traj_steps + (n - d.seg0)) * 4 + (stage - 1)) * 2 * (size_t)N * N
                     : nullptr;
-  // one thread per column x reads (u, v) of both rows, then overwrites
-  // a[x] and a[N + x] only
-  #pragma unroll
-  for (int x = threadIdx.x; x < N; x += G::THREADS) {
-    double pr[2], qr[2];
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-      const int y = y0 + rr;
-      const double2 uv = a[rr * N + x];
-      if (trj) {
-        const size_t o = (size_t)y * N + x;
-        trj[o] = uv.x;
-        trj[(size_t)N * N + o] = uv.y;
-      }
-      if (slot >= 0 && (y % st) == 0 && (x % st) == 0) {
-        const int p = (y / st) * P + x / st;
-        double* o = d.obs + bm * d.obs_stride + ((size_t)slot * P * P + p) * 2;
-        o[0] = uv.x;
-        o[1] = uv.y;
-      }
-      pr[rr] = uv.x * uv.y;
-      qr[rr] = fma(uv.y, uv.y, -uv.x * uv.x);
+  // (u, v) at column x of row y0 + rr: stage-field store, probe gather, and
+  // the products P = u v, Q = v^2 - u^2 as P + i Q
+  auto products = [&](int rr, int x, double2 uv) {
+    const int y = y0 + rr;
+    if (trj) {
+      const size_t o = (size_t)y * N + x;
+      trj[o] = uv.x;
+      trj[(size_t)N * N + o] = uv.y;
     }
-    a[x] = make_double2(pr[0], pr[1]);
-    a[N + x] = make_double2(qr[0], qr[1]);
+    if (slot >= 0 && (y % st) == 0 && (x % st) == 0) {
+      const int p = (y / st) * P + x / st;
+      double* o = d.obs + bm * d.obs_stride + ((size_t)slot * P * P + p) * 2;
+      o[0] = uv.x;
+      o[1] = uv.y;
+    }
+    return make_double2(uv.x * uv.y, fma(uv.y, uv.y, -uv.x * uv.x));
+  };
+  if (flags & F_OBS_ONLY) {  // the final state: stage fields and probes only
+    fft_folded<N, V, +1, 2, G::K>(a, T);
+    for (int u = threadIdx.x; u < 2 * N; u += G::THREADS) products(u / N, u % N, a[u]);
+    return;
   }
-  if (flags & F_OBS_ONLY) return;
-  __syncthreads();
-  fft_folded<N, V, -1, 2, -1, G::K>(a, T);
-  unpack_field_rows<N, V>(a, d.Mn + (size_t)bm * G::Kc * 2 * N, y0);
+  if constexpr (Fusable<N, V>::value) {
+    fft_folded_turn<N, V, 2, G::K, G::K>(a, T, products);
+  } else {
+    fft_folded<N, V, +1, 2, G::K>(a, T);
+    // each position is read and rewritten by one thread only
+#pragma unroll
+    for (int t = 0; t < (2 * N + G::THREADS - 1) / G::THREADS; ++t) {
+      const int u = threadIdx.x + t * G::THREADS;
+      if (u < 2 * N) a[u] = products(u / N, u % N, a[u]);
+    }
+    __syncthreads();
+    fft_folded<N, V, -1, 2, -1, G::K>(a, T);
+  }
+  unpack_row_pairs<N, V>(a, d.Mn + (size_t)bm * G::Kc * 2 * N, y0);
 }
 
 // Column pass of stage `stage`: the advection term
@@ -722,9 +727,9 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_init(Dev d, int mode
 }
 
 // Adjoint row pass of stage `stage` of step n: 2a, b of rows y0, y0+1
-// (inverse transforms along x), rho_u and rho_v with the stored u, v, and
-// their forward transforms along x into Mn (twice, as in the forward row
-// pass).  grid (N/2, B).
+// (inverse transforms along x), rho_u and rho_v with the stored u, v (each
+// row packed as rho_u + i rho_v), and their forward transforms along x into
+// Mn (twice, as in the forward row pass).  grid (N/2, B).
 template <int N, int V = 0>
 __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_rows(Dev d, int n, int stage) {
   using G = Geo<N, V>;
@@ -736,27 +741,27 @@ __global__ void __launch_bounds__(Geo<N, V>::THREADS) k_adj_rows(Dev d, int n, i
   load_fold<N, V>(T, d.fold);
   pack_field_pairs<N, V>(a, d.Mx + (size_t)bm * 2 * N * G::Kc, y0);
   __syncthreads();
-  fft_folded<N, V, +1, 2, G::K>(a, T);
   const double* trj = d.traj + (((size_t)bm * d.traj_steps + (n - d.seg0)) * 4 + (stage - 1)) * 2 * (size_t)N * N;
-  // one thread per column x reads (a, b) of both rows, then writes
-  // rho_u and rho_v of both rows at x
-  #pragma unroll
-  for (int x = threadIdx.x; x < N; x += G::THREADS) {
-    double ru[2], rv[2];
+  // (2a, b) at column x of row y0 + rr -> rho_u + i rho_v with the stored u, v
+  auto rho = [&](int rr, int x, double2 ab) {
+    const size_t o = (size_t)(y0 + rr) * N + x;
+    const double fu = trj[o], fv = trj[(size_t)N * N + o];
+    return make_double2(fma(fv, ab.y, -fu * ab.x), fma(fu, ab.y, fv * ab.x));
+  };
+  if constexpr (Fusable<N, V>::value) {
+    fft_folded_turn<N, V, 2, G::K, G::K>(a, T, rho);
+  } else {
+    fft_folded<N, V, +1, 2, G::K>(a, T);
+    // each position is read and rewritten by one thread only
 #pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-      const double2 ab = a[rr * N + x];  // (2a, b)
-      const size_t o = (size_t)(y0 + rr) * N + x;
-      const double fu = trj[o], fv = trj[(size_t)N * N + o];
-      ru[rr] = fma(fv, ab.y, -fu * ab.x);
-      rv[rr] = fma(fu, ab.y, fv * ab.x);
+    for (int t = 0; t < (2 * N + G::THREADS - 1) / G::THREADS; ++t) {
+      const int u = threadIdx.x + t * G::THREADS;
+      if (u < 2 * N) a[u] = rho(u / N, u % N, a[u]);
     }
-    a[x] = make_double2(ru[0], ru[1]);
-    a[N + x] = make_double2(rv[0], rv[1]);
+    __syncthreads();
+    fft_folded<N, V, -1, 2, -1, G::K>(a, T);
   }
-  __syncthreads();
-  fft_folded<N, V, -1, 2, -1, G::K>(a, T);
-  unpack_field_rows<N, V>(a, d.Mn + (size_t)bm * G::Kc * 2 * N, y0);
+  unpack_row_pairs<N, V>(a, d.Mn + (size_t)bm * G::Kc * 2 * N, y0);
 }
 
 // Adjoint column pass of stage `stage` of step n:
