@@ -94,8 +94,8 @@ def fp64_peak(probe: dict, sms: int) -> dict:
 # (256^2, batch 7), from one ncu capture of the same launch configuration on
 # a 40-step window (per-launch data are the same for any window length);
 # valid only for the kernel sources they were taken from.
-TRAFFIC = {"src_hash": "6353f868f828659d", "adj_rows": 12301824, "adj_cols": 10530816, "fwd_rows": 4973568,
-           "fwd_cols": 10496000}
+TRAFFIC = {"src_hash": "ebf205b24a74b487", "adj_rows": 12301312, "adj_cols": 10530816, "fwd_rows": 4977152,
+           "fwd_cols": 10495744}
 
 
 def src_hash() -> str:
